@@ -1,0 +1,299 @@
+/*
+ * hgrt.h -- C ABI of the GB300 path-calculation library for octree and k-d
+ * tree dust grids (Saftly, Baes & Camps, "Hierarchical octree and k-d tree
+ * grids for 3D radiative transfer simulations").
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked "dev" are CUDA device pointers, "host" are host
+ *     pointers.  The caller owns every buffer it passes; the library owns
+ *     only what it allocates behind an opaque handle (hg_host_grid, hg_grid,
+ *     hg_dmodel, hg_batch) and frees it in the matching hg_free_* call.
+ *   - Calls that take a stream are asynchronous on that stream (NULL means
+ *     the legacy default stream).  Argument, allocation and launch errors
+ *     are returned synchronously as hg_status; a kernel fault surfaces on
+ *     the caller's next synchronisation.  Scratch memory these calls need
+ *     is taken from the CUDA stream-ordered allocator on the same stream
+ *     and released on it before the call returns.
+ *   - Per-ray problems never abort a launch: they are reported as bit
+ *     flags (HG_RAY_*) in the optional per-ray status array.
+ *   - hg_last_error() returns a message for the calling thread's last
+ *     failed call.
+ *   - Arrays of 3-vectors are row-major [n][3] doubles (x, y, z per row).
+ *   - A loaded grid is immutable and may be used from several streams at
+ *     once.
+ */
+#ifndef HGRT_H
+#define HGRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hg_status {
+    HG_OK = 0,
+    HG_EINVAL = 1,      /* bad argument */
+    HG_ENOMEM = 2,      /* host or device allocation failed */
+    HG_ECUDA = 3,       /* a CUDA runtime call failed */
+    HG_EOVERFLOW = 4,   /* output capacity too small */
+    HG_ESTEPLIMIT = 5,  /* some ray hit its step limit */
+    HG_ELOST = 6,       /* some ray found no next cell */
+    HG_EFORMAT = 7,     /* grid description failed validation */
+    HG_EBADINPUT = 8,   /* some ray had a non-finite or zero direction */
+    HG_ENOTFOUND = 9    /* missing CUDA device or symbol */
+} hg_status;
+
+/* per-ray status bits */
+#define HG_RAY_STEPLIMIT 1u /* the walk stopped at max_steps */
+#define HG_RAY_LOST 2u      /* no leaf contained an exit point inside the domain */
+#define HG_RAY_BADINPUT 4u  /* non-finite origin/direction/length or zero direction */
+#define HG_RAY_OVERFLOW 8u  /* emission capacity exceeded; segments truncated */
+
+#define HG_OCTREE 0
+#define HG_KDTREE 1
+
+#define HG_MODEL_CONST 0  /* rho = p[0] */
+#define HG_MODEL_DISK 1   /* rho = p[0] exp(-R/p[1] - |z|/p[2]), R = sqrt(x^2+y^2) */
+#define HG_MODEL_TORUS 2  /* rho0 = p[2] inside (sqrt(x^2+y^2)-p[0])^2 + z^2 < p[1]^2, plus clumps */
+#define HG_MODEL_DYADIC 3 /* piecewise constant on a 2^p[0] lattice, values in table */
+
+#define HG_FP64 0   /* wall test, segment lengths and tau in FP64 */
+#define HG_FP32K 1  /* wall test in FP64; segment lengths and densities cast to FP32,
+                       tau summed in FP32 with Kahan compensation */
+
+typedef void *hg_stream; /* a cudaStream_t */
+
+/* ------------------------------------------------------------------------ density models
+ * Stand-ins for the paper's test models (Sect. 3.1): an exponential disk,
+ * a ring torus with a hard edge plus truncated Gaussian clumps, a uniform
+ * medium and a piecewise-constant lattice.
+ *   torus table: n_table rows of (cx, cy, cz, sigma, A); clump j adds
+ *     A exp(-0.5 r^2/sigma^2) where r^2 < 25 sigma^2, summed in row order.
+ *   dyadic table: 8^L values, index ix + n (iy + n iz), n = 2^L.
+ * m_tot is the total mass inside [lo, hi] used by the mass criterion. */
+typedef struct hg_model {
+    int32_t kind;
+    int32_t n_table;
+    double p[8];
+    const double *table; /* host */
+    double m_tot;
+    double lo[3], hi[3]; /* domain box */
+} hg_model;
+
+/* ------------------------------------------------------------------------ tree construction
+ * Subdivision-stopping criteria of Sect. 2.2 and 4: a node is subdivided
+ * when any enabled test fires (and it is above the maximum level):
+ *   mass fraction   delta = M / m_tot > delta_max      (Sect. 2.2, Eq. 1)
+ *   optical depth   kappa M sqrt(a^2+b^2+c^2)/(abc) > tau_max   (Eq. 2)
+ *   dispersion      q = (rho_max - rho_min)/rho_max > q_max     (Eq. 3)
+ * M = V * mean of rho_t at n_ran positions drawn uniformly in the node
+ * (Eq. 1) with SplitMix64 keyed by the node's box, so that a node's samples
+ * do not depend on the build order.  max_level counts octree levels; a k-d
+ * tree may be 3*max_level splits deep (Sect. 2.1). */
+typedef struct hg_build_params {
+    int32_t kind; /* HG_OCTREE or HG_KDTREE */
+    int32_t use_delta, use_tau, use_q;
+    double delta_max, tau_max, q_max, kappa;
+    int32_t max_level; /* 0..20 */
+    int32_t n_ran;     /* >= 1 */
+    uint64_t seed;
+    int64_t max_nodes; /* 0 = unlimited; otherwise the build fails with HG_EOVERFLOW beyond it */
+} hg_build_params;
+
+/* Flat description of a grid: the node list of Sect. 2.2 (root first,
+ * children contiguous: 8 for an octree in x-fastest order, 2 for a k-d
+ * tree, lower child first), leaf densities, and the six neighbor lists per
+ * leaf of Sect. 2.3 (walls -x,+x,-y,+y,-z,+z; each list sorted by
+ * decreasing overlap area, ties by ascending leaf id).  All host pointers,
+ * read only during the call that receives them. */
+typedef struct hg_grid_desc {
+    int32_t kind;
+    int32_t reserved;
+    int64_t n_nodes;
+    int64_t n_leaves;
+    const double *node_lo;       /* [n_nodes][3] */
+    const double *node_hi;       /* [n_nodes][3] */
+    const int32_t *child_first;  /* [n_nodes], -1 for a leaf */
+    const int32_t *node_leaf;    /* [n_nodes], leaf id or -1; leaf ids follow list order */
+    const double *leaf_rho;      /* [n_leaves] */
+    const int64_t *nbr_off;      /* [6*n_leaves+1], list of wall w of leaf i = nbr_off[6i+w] .. nbr_off[6i+w+1] */
+    const int32_t *nbr_id;       /* [nbr_off[6*n_leaves]] */
+} hg_grid_desc;
+
+/* Extra per-node builder output (host arrays owned by the hg_host_grid). */
+typedef struct hg_host_nodes {
+    const int32_t *level;  /* [n_nodes][3] per-axis subdivision level */
+    const int64_t *index;  /* [n_nodes][3] per-axis integer position at that level */
+    const double *mass;    /* [n_nodes] Eq. 1 */
+    const double *delta;   /* [n_nodes] M / m_tot */
+    const double *tau;     /* [n_nodes] Eq. 2 */
+    const double *q;       /* [n_nodes] Eq. 3 */
+} hg_host_nodes;
+
+typedef struct hg_host_grid hg_host_grid;
+
+/* Build a tree on the host with n_threads threads (<= 0: all cores).
+ * Deterministic: the result does not depend on n_threads. */
+hg_status hg_build_grid(const hg_model *model, const hg_build_params *params, int32_t n_threads,
+                        hg_host_grid **out);
+/* View the built grid as a description (pointers stay valid until hg_free_host_grid). */
+hg_status hg_host_grid_desc(const hg_host_grid *g, hg_grid_desc *out);
+hg_status hg_host_grid_nodes(const hg_host_grid *g, hg_host_nodes *out);
+void hg_free_host_grid(hg_host_grid *g);
+
+/* ------------------------------------------------------------------------ device grid */
+typedef struct hg_grid hg_grid;
+
+typedef struct hg_grid_info {
+    int32_t kind;
+    int32_t max_depth;      /* deepest node in the node list (k-d splits or octree levels) */
+    int64_t n_nodes, n_leaves;
+    int64_t n_tail;         /* stored neighbor entries beyond each wall's first */
+    int64_t device_bytes;   /* HBM held by the grid */
+    int64_t long_walls;     /* walls whose list is longer than the scan limit (searched top-down) */
+    double lo[3], hi[3];
+} hg_grid_info;
+
+/* Upload a grid.  With validate != 0 the description is checked first
+ * (links in range, children tiling their parent, leaf ids, every neighbor
+ * list adjacent to its wall and tiling it); a failure returns HG_EFORMAT.
+ * Needs a current CUDA device. */
+hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate, hg_grid **out);
+void hg_free_grid(hg_grid *g);
+hg_status hg_grid_get_info(const hg_grid *g, hg_grid_info *out);
+
+/* ------------------------------------------------------------------------ path calculation
+ * A path is x(t) = o + t d for t in [t_start, t_end]: t_start = 0 for an
+ * origin inside the domain, else the entry time of the slab test; t_end is
+ * the domain exit, or s_max if given and smaller.  The result is the
+ * ordered list of leaves whose interior the path crosses with the length
+ * ds inside each, and tau = kappa * sum rho_leaf ds (Sect. 2.3, 3.2).  The
+ * first leaf comes from a top-down descent; every later one from the exit
+ * wall's neighbor list (Sect. 2.3), the list's first entry being stored in
+ * the leaf itself, with a top-down descent when no listed neighbor
+ * contains the exit point (edge and corner exits) or the list is long.
+ *
+ * FP64 arithmetic, no fused multiply-add, as in this contract:
+ *   invk_a = 1/d_a (d_a == +-0: axis a never exits);
+ *   t_a = (wall_a - o_a) * invk_a for the wall ahead on each axis; exit at
+ *   the smallest, ties to the lower axis; t_end wins only when smaller;
+ *   exit times are never below the current time; ds = t_exit - t_cur and
+ *   segments with ds == 0 are skipped (not emitted, not counted);
+ *   exit point p_a = wall_a, p_b = o_b + d_b t_exit clamped to the leaf;
+ *   p lies in box [l, h] iff per axis l < p < h, p == l with d >= 0, or
+ *   p == h with d < 0 (the domain's upper face also with d == 0);
+ *   FP64 tau = kappa * (sum of rho*ds, left to right).
+ * Directions are used as given (not normalised); s_max is in the same t. */
+typedef struct hg_trace_opts {
+    int32_t precision;   /* HG_FP64 or HG_FP32K */
+    int32_t block;       /* threads per block; 0 = tuned or default */
+    int32_t smem_nodes;  /* top tree nodes staged in shared memory; -1 = tuned or default */
+    int32_t schedule;    /* 0 = tuned or default, 1 = one ray per thread, 2 = persistent with warp refill */
+    int64_t max_steps;   /* per-ray step limit; 0 = 4 * n_leaves + 64 */
+} hg_trace_opts;
+
+/* tau: dev f64[n] (HG_FP64) or f32[n] (HG_FP32K).  ncross: dev i32[n],
+ * number of segments with ds > 0.  ray_status: dev u8[n] or NULL.
+ * o, d: dev f64[n][3]; s_max: dev f64[n] or NULL. */
+hg_status hg_trace_rays(const hg_grid *g, int64_t n, const double *o, const double *d, const double *s_max,
+                        double kappa, const hg_trace_opts *opts, void *tau, int32_t *ncross,
+                        uint8_t *ray_status, hg_stream stream);
+
+/* As hg_trace_rays, with the leaf densities read from rho (dev f64[n_leaves])
+ * instead of the grid's own: tau is linear in rho, and this is the forward
+ * pass whose adjoint is hg_tau_gradient. */
+hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double *o, const double *d, const double *s_max,
+                            double kappa, const double *rho, const hg_trace_opts *opts, void *tau,
+                            int32_t *ncross, uint8_t *ray_status, hg_stream stream);
+
+/* Exclusive scan: seg_off[0] = 0, seg_off[i+1] = seg_off[i] + count[i]
+ * (dev i32[n] -> dev i64[n+1]). */
+hg_status hg_scan_offsets(int64_t n, const int32_t *count, int64_t *seg_off, hg_stream stream);
+
+/* Emission pass (Sect. 2.3 "ordered list of dust cells"): writes ray i's
+ * segments to seg_cell[seg_off[i] ..] (dev i32, leaf ids) and seg_ds (dev
+ * f64, or f32 under HG_FP32K) in path order.  seg_off comes from
+ * hg_scan_offsets over the ncross of hg_trace_rays with the same inputs;
+ * entries at or beyond seg_capacity are not written and flag the ray
+ * HG_RAY_OVERFLOW. */
+hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o, const double *d, const double *s_max,
+                        const hg_trace_opts *opts, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
+                        int64_t seg_capacity, uint8_t *ray_status, hg_stream stream);
+
+/* Grid density at points (Sect. 3.2, rho_g): top-down location with the
+ * half-open rule above for a zero direction; cell = -1 and rho = 0 for
+ * points outside the domain.  pts dev f64[n][3], cell dev i32[n] (or
+ * NULL), rho dev f64[n]. */
+hg_status hg_sample_density(const hg_grid *g, int64_t n, const double *pts, int32_t *cell, double *rho,
+                            hg_stream stream);
+
+/* Adjoint of tau with respect to the leaf densities: for L = sum_r w_r tau_r,
+ * grad_rho[c] += kappa * sum over segments s of ray r inside c of w_r ds_s.
+ * w dev f32[n]; grad_rho dev f32[n_leaves] (grad_precision 1, FP32 atomics)
+ * or f64[n_leaves] (grad_precision 0, FP64 atomics), ACCUMULATED. */
+hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *o, const double *d, const double *s_max,
+                          double kappa, const float *w, int32_t grad_precision, void *grad_rho,
+                          const hg_trace_opts *opts, hg_stream stream);
+
+/* OR of the per-ray status bits into *out_bits (dev u32, overwritten). */
+hg_status hg_reduce_status(int64_t n, const uint8_t *ray_status, uint32_t *out_bits, hg_stream stream);
+/* Map OR-ed ray bits to one call-level status (host). */
+hg_status hg_status_from_bits(uint32_t bits);
+
+/* ------------------------------------------------------------------------ grid-quality metrics (Sect. 3.2) */
+typedef struct hg_dmodel hg_dmodel;
+
+/* Upload a density model for the true density rho_t and true optical depth. */
+hg_status hg_load_model(const hg_model *model, hg_dmodel **out);
+void hg_free_model(hg_dmodel *m);
+/* rho_t at points: pts dev f64[n][3] -> rho dev f64[n]. */
+hg_status hg_model_density(const hg_dmodel *m, int64_t n, const double *pts, double *rho, hg_stream stream);
+/* tau_t = kappa * integral_0^len rho_t(o + t d) dt by adaptive 15-point
+ * Gauss-Kronrod quadrature with breakpoints at the model's kinks and edges,
+ * local relative tolerance rtol.  Directions must be unit vectors. */
+hg_status hg_model_tau(const hg_dmodel *m, int64_t n, const double *o, const double *d, const double *len,
+                       double kappa, double rtol, double *tau, hg_stream stream);
+/* Statistics of x = a - b (dev f64[n] each): out dev f64[3] = {n, mean, population std},
+ * two passes in FP64 (Delta-rho and Delta-tau are the std of rho_t - rho_g and tau_t - tau_g). */
+hg_status hg_diff_stats(int64_t n, const double *a, const double *b, double *out, hg_stream stream);
+/* Sum of ncross (dev i32[n]) into *out (dev i64): <N_cross> = *out / n (Sect. 3.2). */
+hg_status hg_sum_i32(int64_t n, const int32_t *x, int64_t *out, hg_stream stream);
+
+/* ------------------------------------------------------------------------ batched launch
+ * Many grids of uneven size, each with its own ray range, traced in one
+ * persistent launch: ray chunks of every grid form one work list that
+ * resident blocks drain through an atomic counter, larger grids first.
+ * ray_begin (host i64[n_grids+1]) splits the concatenated ray and output
+ * arrays by grid.  The batch holds a device table of the grids (which
+ * must outlive it) and a reusable work counter; hg_batch_trace may be
+ * captured into a CUDA graph once and replayed. */
+typedef struct hg_batch hg_batch;
+hg_status hg_batch_create(int32_t n_grids, const hg_grid *const *grids, const int64_t *ray_begin,
+                          int32_t chunk, hg_batch **out);
+void hg_batch_free(hg_batch *b);
+hg_status hg_batch_trace(hg_batch *b, const double *o, const double *d, const double *s_max, double kappa,
+                         const hg_trace_opts *opts, void *tau, int32_t *ncross, uint8_t *ray_status,
+                         hg_stream stream);
+
+/* ------------------------------------------------------------------------ autotuner
+ * Time candidate launch configurations (threads per block, shared-memory
+ * tree nodes, schedule) on a sample of n rays with CUDA events, keep the
+ * fastest for this grid and precision (used when opts fields are 0 / -1),
+ * and return it in *best.  Synchronises the stream. */
+hg_status hg_autotune(hg_grid *g, int64_t n, const double *o, const double *d, int32_t precision,
+                      hg_trace_opts *best, float *best_ms, hg_stream stream);
+
+/* ------------------------------------------------------------------------ misc */
+const char *hg_status_str(hg_status s);
+const char *hg_last_error(void);
+int32_t hg_version(void);
+/* Number of kernel launches this library issued in the calling process. */
+int64_t hg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HGRT_H */

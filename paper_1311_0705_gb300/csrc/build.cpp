@@ -1,0 +1,441 @@
+// Host tree construction (Sect. 2.2, 4.1, 4.2) and neighbor lists (Sect. 2.3).
+//
+// The node list of Sect. 2.2 is built breadth first: the paper's single
+// loop over a list that appends children at its end visits nodes level by
+// level, so each level is evaluated in parallel and its children appended
+// in parent order afterwards, which yields the same list.  Every node's
+// Monte Carlo samples (Eq. 1) come from a SplitMix64 counter stream keyed
+// by the node's box, so the result does not depend on the thread count.
+//
+// Neighbor lists are found per leaf wall by a descent over the tree in
+// exact integer lattice coordinates and sorted by decreasing overlap area
+// (ties by ascending leaf id).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <memory>
+#include <thread>
+
+#include "hg_internal.h"
+
+namespace {
+
+constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
+
+// SplitMix64 output function (Steele, Lea & Flood 2014).
+inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+inline uint64_t box_key(uint64_t seed, const int32_t *l, const int64_t *i) {
+    uint64_t lv = (uint64_t)l[0] | ((uint64_t)l[1] << 8) | ((uint64_t)l[2] << 16);
+    uint64_t k = mix64(seed + kGamma * (1ULL + lv));
+    k = mix64(k + kGamma * (1ULL + (uint64_t)i[0]));
+    k = mix64(k + kGamma * (1ULL + (uint64_t)i[1]));
+    return mix64(k + kGamma * (1ULL + (uint64_t)i[2]));
+}
+
+inline double unit_draw(uint64_t key, uint64_t j) {
+    return (double)(mix64(key + kGamma * (j + 1ULL)) >> 11) * 0x1.0p-53;
+}
+
+template <class F>
+void parallel_for(int64_t n, int threads, F &&fn) {
+    if (n <= 0) return;
+    if (threads <= 1 || n < 64) {
+        fn(0, n);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    const int64_t chunk = std::max<int64_t>(16, n / (threads * 16));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; t++)
+        pool.emplace_back([&]() {
+            for (;;) {
+                int64_t a = next.fetch_add(chunk);
+                if (a >= n) break;
+                fn(a, std::min(n, a + chunk));
+            }
+        });
+    for (auto &th : pool) th.join();
+}
+
+// Density model with a uniform spatial index over the clumps.  The sum
+// visits a point's candidate clumps in ascending order and applies the
+// same cut-off test as a plain loop over all clumps, so the value is the
+// same double.
+struct HostModel {
+    hg_model m{};
+    std::vector<double> table;
+    int G = 0;
+    std::vector<int32_t> cell_off, cell_ids;
+
+    void init(const hg_model &src) {
+        m = src;
+        size_t per = (src.kind == HG_MODEL_TORUS) ? 5 : 1;
+        table.assign(src.table, src.table + (size_t)std::max(0, src.n_table) * per);
+        m.table = table.data();
+        if (src.kind == HG_MODEL_TORUS && src.n_table > 0) build_index();
+    }
+
+    void build_index() {
+        G = 48;
+        const int64_t nc = (int64_t)G * G * G;
+        std::vector<std::vector<int32_t>> lists((size_t)nc);
+        double ext[3];
+        for (int a = 0; a < 3; a++) ext[a] = m.hi[a] - m.lo[a];
+        for (int32_t j = 0; j < m.n_table; j++) {
+            const double *c = &table[5 * (size_t)j];
+            double rad = 5.0 * c[3] * (1.0 + 1e-9) + 1e-12;
+            int lo[3], hi[3];
+            for (int a = 0; a < 3; a++) {
+                lo[a] = std::max(0, (int)std::floor((c[a] - rad - m.lo[a]) / ext[a] * G) - 1);
+                hi[a] = std::min(G - 1, (int)std::floor((c[a] + rad - m.lo[a]) / ext[a] * G) + 1);
+            }
+            for (int z = lo[2]; z <= hi[2]; z++)
+                for (int y = lo[1]; y <= hi[1]; y++)
+                    for (int x = lo[0]; x <= hi[0]; x++) {
+                        // conservative sphere-box test (cell grown by a relative margin)
+                        int ix[3] = {x, y, z};
+                        double d2 = 0.0;
+                        for (int a = 0; a < 3; a++) {
+                            double b0 = m.lo[a] + ext[a] * ((double)ix[a] / G) - 1e-9 * ext[a];
+                            double b1 = m.lo[a] + ext[a] * ((double)(ix[a] + 1) / G) + 1e-9 * ext[a];
+                            double v = c[a] < b0 ? b0 - c[a] : (c[a] > b1 ? c[a] - b1 : 0.0);
+                            d2 += v * v;
+                        }
+                        if (d2 <= rad * rad) lists[(size_t)x + G * ((size_t)y + G * z)].push_back(j);
+                    }
+        }
+        cell_off.assign((size_t)nc + 1, 0);
+        for (int64_t c = 0; c < nc; c++) cell_off[c + 1] = cell_off[c] + (int32_t)lists[c].size();
+        cell_ids.resize((size_t)cell_off[nc]);
+        for (int64_t c = 0; c < nc; c++) std::copy(lists[c].begin(), lists[c].end(), cell_ids.begin() + cell_off[c]);
+    }
+
+    double rho(double x, double y, double z) const {
+        switch (m.kind) {
+        case HG_MODEL_CONST:
+            return m.p[0];
+        case HG_MODEL_DISK: {
+            double R = std::sqrt(x * x + y * y);
+            double e = -(R / m.p[1]) - (std::fabs(z) / m.p[2]);
+            return m.p[0] * std::exp(e);
+        }
+        case HG_MODEL_TORUS: {
+            double s = std::sqrt(x * x + y * y) - m.p[0];
+            double v = (s * s + z * z < m.p[1] * m.p[1]) ? m.p[2] : 0.0;
+            if (m.n_table <= 0) return v;
+            double pos[3] = {x, y, z};
+            int ix[3];
+            for (int a = 0; a < 3; a++) {
+                int q = (int)std::floor((pos[a] - m.lo[a]) / (m.hi[a] - m.lo[a]) * G);
+                ix[a] = q < 0 ? 0 : (q >= G ? G - 1 : q);
+            }
+            size_t c = (size_t)ix[0] + G * ((size_t)ix[1] + G * ix[2]);
+            for (int32_t e = cell_off[c]; e < cell_off[c + 1]; e++) {
+                const double *cl = &table[5 * (size_t)cell_ids[e]];
+                double dx = x - cl[0], dy = y - cl[1], dz = z - cl[2];
+                double r2 = dx * dx + dy * dy + dz * dz;
+                double s2 = cl[3] * cl[3];
+                if (r2 < 25.0 * s2) v += cl[4] * std::exp(-0.5 * (r2 / s2));
+            }
+            return v;
+        }
+        case HG_MODEL_DYADIC: {
+            int L = (int)m.p[0];
+            int64_t n = (int64_t)1 << L;
+            double pos[3] = {x, y, z};
+            int64_t ix[3];
+            for (int a = 0; a < 3; a++) {
+                double f = (pos[a] - m.lo[a]) / (m.hi[a] - m.lo[a]) * (double)n;
+                int64_t q = (int64_t)std::floor(f);
+                ix[a] = q < 0 ? 0 : (q > n - 1 ? n - 1 : q);
+            }
+            return m.table[ix[0] + n * (ix[1] + n * ix[2])];
+        }
+        }
+        return 0.0;
+    }
+
+    // lo + (hi - lo) * i / 2^l on axis a, the top end being hi itself
+    double bound(int a, int64_t i, int32_t l) const {
+        if (i == ((int64_t)1 << l)) return m.hi[a];
+        return m.lo[a] + (m.hi[a] - m.lo[a]) * std::ldexp((double)i, -l);
+    }
+};
+
+struct Stats {
+    double rho, mass, delta, tau, q;
+    bool sub;
+};
+
+Stats eval_node(const HostModel &M, const hg_build_params &P, const int32_t *l, const int64_t *i, int32_t depth) {
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = M.bound(a, i[a], l[a]);
+        hi[a] = M.bound(a, i[a] + 1, l[a]);
+    }
+    const uint64_t key = box_key(P.seed, l, i);
+    double S = 0.0, rmin = 0.0, rmax = 0.0;
+    for (int32_t s = 0; s < P.n_ran; s++) {
+        double x = lo[0] + unit_draw(key, 3ULL * s) * (hi[0] - lo[0]);
+        double y = lo[1] + unit_draw(key, 3ULL * s + 1) * (hi[1] - lo[1]);
+        double z = lo[2] + unit_draw(key, 3ULL * s + 2) * (hi[2] - lo[2]);
+        double r = M.rho(x, y, z);
+        S += r;
+        if (s == 0 || r < rmin) rmin = r;
+        if (s == 0 || r > rmax) rmax = r;
+    }
+    Stats st;
+    double a = hi[0] - lo[0], b = hi[1] - lo[1], c = hi[2] - lo[2];
+    double V = a * b * c;
+    st.rho = S / (double)P.n_ran;
+    st.mass = V * st.rho;
+    st.delta = st.mass / M.m.m_tot;
+    st.tau = P.kappa * st.mass * std::sqrt(a * a + b * b + c * c) / (a * b * c);
+    st.q = (rmax > 0.0) ? (rmax - rmin) / rmax : 0.0;
+    bool at_max = (P.kind == HG_OCTREE) ? (l[0] >= P.max_level) : (depth >= 3 * P.max_level);
+    bool sub = (P.use_delta && st.delta > P.delta_max) || (P.use_tau && st.tau > P.tau_max) ||
+               (P.use_q && st.q > P.q_max);
+    st.sub = sub && !at_max;
+    return st;
+}
+
+}  // namespace
+
+struct hg_host_grid {
+    int32_t kind = 0;
+    std::vector<int32_t> lvl;   // [3n]
+    std::vector<int64_t> idx;   // [3n]
+    std::vector<int32_t> child; // [n]
+    std::vector<int32_t> leaf;  // [n]
+    std::vector<double> lo, hi; // [3n]
+    std::vector<double> rho, mass, delta, tau, q;  // [n]
+    std::vector<double> leaf_rho;
+    std::vector<int64_t> leaf_node;
+    std::vector<int64_t> nbr_off;
+    std::vector<int32_t> nbr_id;
+};
+
+namespace {
+
+// Neighbor lists in lattice units of the finest per-axis level.
+void build_neighbors(hg_host_grid &G, int threads) {
+    const int64_t n = (int64_t)G.child.size();
+    const int64_t nl = (int64_t)G.leaf_node.size();
+    int32_t Lm = 0;
+    for (int32_t v : G.lvl) Lm = std::max(Lm, v);
+    const int64_t top = (int64_t)1 << Lm;
+    auto ibox = [&](int64_t nd, int a, int64_t &lo, int64_t &hi) {
+        int32_t l = G.lvl[3 * nd + a];
+        lo = G.idx[3 * nd + a] << (Lm - l);
+        hi = (G.idx[3 * nd + a] + 1) << (Lm - l);
+    };
+    const int nch = (G.kind == HG_OCTREE) ? 8 : 2;
+    // visit every leaf across wall w of leaf node ln; fn(leaf id, area)
+    auto walk = [&](int64_t ln, int w, std::vector<int64_t> &stack, auto &&fn) {
+        const int a = w >> 1, s = w & 1;
+        int64_t L[3], H[3];
+        for (int b = 0; b < 3; b++) ibox(ln, b, L[b], H[b]);
+        const int64_t P = s ? H[a] : L[a];
+        if ((s && P == top) || (!s && P == 0)) return;
+        stack.clear();
+        stack.push_back(0);
+        while (!stack.empty()) {
+            int64_t nd = stack.back();
+            stack.pop_back();
+            int64_t nlo[3], nhi[3];
+            for (int b = 0; b < 3; b++) ibox(nd, b, nlo[b], nhi[b]);
+            bool across = s ? (nlo[a] <= P && P < nhi[a]) : (nlo[a] < P && P <= nhi[a]);
+            if (!across) continue;
+            int64_t area = 1;
+            bool ok = true;
+            for (int b = 0; b < 3; b++) {
+                if (b == a) continue;
+                int64_t ov = std::min(nhi[b], H[b]) - std::max(nlo[b], L[b]);
+                if (ov <= 0) { ok = false; break; }
+                area *= ov;
+            }
+            if (!ok) continue;
+            if (G.child[nd] < 0) {
+                fn(G.leaf[nd], area);
+            } else {
+                for (int c = nch - 1; c >= 0; c--) stack.push_back(G.child[nd] + c);
+            }
+        }
+    };
+    std::vector<int64_t> counts((size_t)nl * 6, 0);
+    parallel_for(nl, threads, [&](int64_t a0, int64_t a1) {
+        std::vector<int64_t> stack;
+        for (int64_t i = a0; i < a1; i++)
+            for (int w = 0; w < 6; w++) {
+                int64_t c = 0;
+                walk(G.leaf_node[i], w, stack, [&](int32_t, int64_t) { c++; });
+                counts[6 * i + w] = c;
+            }
+    });
+    G.nbr_off.assign((size_t)nl * 6 + 1, 0);
+    for (int64_t j = 0; j < nl * 6; j++) G.nbr_off[j + 1] = G.nbr_off[j] + counts[j];
+    G.nbr_id.assign((size_t)G.nbr_off[nl * 6], 0);
+    parallel_for(nl, threads, [&](int64_t a0, int64_t a1) {
+        std::vector<int64_t> stack;
+        std::vector<std::pair<int64_t, int32_t>> buf;
+        for (int64_t i = a0; i < a1; i++)
+            for (int w = 0; w < 6; w++) {
+                buf.clear();
+                walk(G.leaf_node[i], w, stack, [&](int32_t id, int64_t area) { buf.emplace_back(-area, id); });
+                std::sort(buf.begin(), buf.end());
+                int64_t o = G.nbr_off[6 * i + w];
+                for (size_t e = 0; e < buf.size(); e++) G.nbr_id[o + e] = buf[e].second;
+            }
+    });
+    (void)n;
+}
+
+}  // namespace
+
+extern "C" hg_status hg_build_grid(const hg_model *model, const hg_build_params *params, int32_t n_threads,
+                                   hg_host_grid **out) {
+    if (!model || !params || !out) {
+        hg::set_error("hg_build_grid: null argument");
+        return HG_EINVAL;
+    }
+    *out = nullptr;
+    const hg_build_params P = *params;
+    if (P.kind != HG_OCTREE && P.kind != HG_KDTREE) { hg::set_error("bad tree kind %d", P.kind); return HG_EINVAL; }
+    if (P.n_ran < 1 || P.max_level < 0 || P.max_level > 20) {
+        hg::set_error("hg_build_grid: n_ran must be >= 1 and max_level in 0..20");
+        return HG_EINVAL;
+    }
+    if (!(model->m_tot > 0.0)) { hg::set_error("hg_build_grid: m_tot must be > 0"); return HG_EINVAL; }
+    if (model->kind < HG_MODEL_CONST || model->kind > HG_MODEL_DYADIC) {
+        hg::set_error("hg_build_grid: bad model kind %d", model->kind);
+        return HG_EINVAL;
+    }
+    if ((model->kind == HG_MODEL_TORUS || model->kind == HG_MODEL_DYADIC) && model->n_table > 0 && !model->table) {
+        hg::set_error("hg_build_grid: model table missing");
+        return HG_EINVAL;
+    }
+    for (int a = 0; a < 3; a++)
+        if (!(model->hi[a] > model->lo[a])) { hg::set_error("hg_build_grid: empty domain"); return HG_EINVAL; }
+    int threads = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+
+    std::unique_ptr<hg_host_grid> G(new hg_host_grid());
+    HostModel M;
+    try {
+        M.init(*model);
+        G->kind = P.kind;
+        auto push = [&](const int32_t *l, const int64_t *i) {
+            for (int a = 0; a < 3; a++) {
+                G->lvl.push_back(l[a]);
+                G->idx.push_back(i[a]);
+                G->lo.push_back(M.bound(a, i[a], l[a]));
+                G->hi.push_back(M.bound(a, i[a] + 1, l[a]));
+            }
+            G->child.push_back(-1);
+            G->leaf.push_back(-1);
+        };
+        int32_t l0[3] = {0, 0, 0};
+        int64_t i0[3] = {0, 0, 0};
+        push(l0, i0);
+        int64_t begin = 0;
+        std::vector<Stats> st;
+        while (begin < (int64_t)G->child.size()) {
+            const int64_t end = (int64_t)G->child.size();
+            st.assign((size_t)(end - begin), Stats{});
+            parallel_for(end - begin, threads, [&](int64_t a0, int64_t a1) {
+                for (int64_t j = a0; j < a1; j++) {
+                    const int64_t nd = begin + j;
+                    const int32_t *l = &G->lvl[3 * nd];
+                    const int64_t *i = &G->idx[3 * nd];
+                    int32_t depth = (P.kind == HG_OCTREE) ? l[0] : l[0] + l[1] + l[2];
+                    st[j] = eval_node(M, P, l, i, depth);
+                }
+            });
+            for (int64_t j = 0; j < end - begin; j++) {
+                G->rho.push_back(st[j].rho);
+                G->mass.push_back(st[j].mass);
+                G->delta.push_back(st[j].delta);
+                G->tau.push_back(st[j].tau);
+                G->q.push_back(st[j].q);
+            }
+            for (int64_t nd = begin; nd < end; nd++) {
+                if (!st[nd - begin].sub) continue;
+                const int nch = (P.kind == HG_OCTREE) ? 8 : 2;
+                if (P.max_nodes > 0 && (int64_t)G->child.size() + nch > P.max_nodes) {
+                    hg::set_error("hg_build_grid: more than max_nodes=%lld nodes", (long long)P.max_nodes);
+                    return HG_EOVERFLOW;
+                }
+                if ((int64_t)G->child.size() + nch > INT32_MAX) {
+                    hg::set_error("hg_build_grid: node count exceeds int32 ids");
+                    return HG_EOVERFLOW;
+                }
+                G->child[nd] = (int32_t)G->child.size();
+                int32_t l[3] = {G->lvl[3 * nd], G->lvl[3 * nd + 1], G->lvl[3 * nd + 2]};
+                int64_t i[3] = {G->idx[3 * nd], G->idx[3 * nd + 1], G->idx[3 * nd + 2]};
+                const int axis = (P.kind == HG_OCTREE) ? -1 : (l[0] + l[1] + l[2]) % 3;
+                for (int c = 0; c < nch; c++) {
+                    int32_t lc[3] = {l[0], l[1], l[2]};
+                    int64_t ic[3] = {i[0], i[1], i[2]};
+                    if (axis < 0) {
+                        for (int a = 0; a < 3; a++) {
+                            lc[a] = l[a] + 1;
+                            ic[a] = 2 * i[a] + ((c >> a) & 1);
+                        }
+                    } else {
+                        lc[axis] = l[axis] + 1;
+                        ic[axis] = 2 * i[axis] + c;
+                    }
+                    push(lc, ic);
+                }
+            }
+            begin = end;
+        }
+        const int64_t n = (int64_t)G->child.size();
+        for (int64_t nd = 0; nd < n; nd++)
+            if (G->child[nd] < 0) {
+                G->leaf[nd] = (int32_t)G->leaf_node.size();
+                G->leaf_node.push_back(nd);
+                G->leaf_rho.push_back(G->rho[nd]);
+            }
+        build_neighbors(*G, threads);
+    } catch (const std::bad_alloc &) {
+        hg::set_error("hg_build_grid: out of host memory");
+        return HG_ENOMEM;
+    }
+    *out = G.release();
+    return HG_OK;
+}
+
+extern "C" hg_status hg_host_grid_desc(const hg_host_grid *g, hg_grid_desc *out) {
+    if (!g || !out) { hg::set_error("hg_host_grid_desc: null argument"); return HG_EINVAL; }
+    out->kind = g->kind;
+    out->reserved = 0;
+    out->n_nodes = (int64_t)g->child.size();
+    out->n_leaves = (int64_t)g->leaf_node.size();
+    out->node_lo = g->lo.data();
+    out->node_hi = g->hi.data();
+    out->child_first = g->child.data();
+    out->node_leaf = g->leaf.data();
+    out->leaf_rho = g->leaf_rho.data();
+    out->nbr_off = g->nbr_off.data();
+    out->nbr_id = g->nbr_id.data();
+    return HG_OK;
+}
+
+extern "C" hg_status hg_host_grid_nodes(const hg_host_grid *g, hg_host_nodes *out) {
+    if (!g || !out) { hg::set_error("hg_host_grid_nodes: null argument"); return HG_EINVAL; }
+    out->level = g->lvl.data();
+    out->index = g->idx.data();
+    out->mass = g->mass.data();
+    out->delta = g->delta.data();
+    out->tau = g->tau.data();
+    out->q = g->q.data();
+    return HG_OK;
+}
+
+extern "C" void hg_free_host_grid(hg_host_grid *g) { delete g; }

@@ -1,0 +1,326 @@
+// Grid upload (hg_load_grid): validation of a grid description, derivation
+// of the packed leaf records and descent nodes, and the copy to HBM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "hg_internal.h"
+
+namespace {
+
+constexpr int kScanLimit = 16;  // neighbor lists longer than this are searched top-down
+
+hg_status cuda_fail(cudaError_t e, const char *what) {
+    hg::set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HG_ENOMEM : HG_ECUDA;
+}
+
+hg_status validate(const hg_grid_desc &D) {
+    const int64_t n = D.n_nodes, nl = D.n_leaves;
+    const int nch = (D.kind == HG_OCTREE) ? 8 : 2;
+    std::vector<int32_t> parent((size_t)n, -1);
+    int64_t next_leaf = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const double *lo = D.node_lo + 3 * i, *hi = D.node_hi + 3 * i;
+        for (int a = 0; a < 3; a++)
+            if (!(std::isfinite(lo[a]) && std::isfinite(hi[a]) && lo[a] < hi[a])) {
+                hg::set_error("node %lld has an empty or non-finite box", (long long)i);
+                return HG_EFORMAT;
+            }
+        const int32_t c = D.child_first[i];
+        if (c < 0) {
+            if (D.node_leaf[i] != next_leaf) {
+                hg::set_error("node %lld: leaf ids must follow list order", (long long)i);
+                return HG_EFORMAT;
+            }
+            next_leaf++;
+            continue;
+        }
+        if (D.node_leaf[i] != -1) {
+            hg::set_error("internal node %lld carries a leaf id", (long long)i);
+            return HG_EFORMAT;
+        }
+        if (c <= i || (int64_t)c + nch > n) {
+            hg::set_error("node %lld: child index %d out of order or range", (long long)i, c);
+            return HG_EFORMAT;
+        }
+        for (int j = 0; j < nch; j++) {
+            if (parent[c + j] != -1) {
+                hg::set_error("node %d has two parents", c + j);
+                return HG_EFORMAT;
+            }
+            parent[c + j] = (int32_t)i;
+        }
+        // children tile the parent
+        const double *c0hi = D.node_hi + 3 * (int64_t)c;
+        if (D.kind == HG_OCTREE) {
+            for (int j = 0; j < 8; j++) {
+                const double *clo = D.node_lo + 3 * ((int64_t)c + j), *chi = D.node_hi + 3 * ((int64_t)c + j);
+                for (int a = 0; a < 3; a++) {
+                    double s = c0hi[a];
+                    bool up = (j >> a) & 1;
+                    double elo = up ? s : lo[a], ehi = up ? hi[a] : s;
+                    if (clo[a] != elo || chi[a] != ehi || !(lo[a] < s && s < hi[a])) {
+                        hg::set_error("octree children of node %lld do not tile it", (long long)i);
+                        return HG_EFORMAT;
+                    }
+                }
+            }
+        } else {
+            int ax = -1;
+            for (int a = 0; a < 3; a++)
+                if (c0hi[a] != hi[a]) ax = (ax == -1) ? a : 3;
+            if (ax < 0 || ax > 2) {
+                hg::set_error("k-d node %lld: children must split exactly one axis", (long long)i);
+                return HG_EFORMAT;
+            }
+            const double s = c0hi[ax];
+            for (int j = 0; j < 2; j++) {
+                const double *clo = D.node_lo + 3 * ((int64_t)c + j), *chi = D.node_hi + 3 * ((int64_t)c + j);
+                for (int a = 0; a < 3; a++) {
+                    double elo = lo[a], ehi = hi[a];
+                    if (a == ax) {
+                        elo = j ? s : lo[a];
+                        ehi = j ? hi[a] : s;
+                    }
+                    if (clo[a] != elo || chi[a] != ehi || !(lo[ax] < s && s < hi[ax])) {
+                        hg::set_error("k-d children of node %lld do not tile it", (long long)i);
+                        return HG_EFORMAT;
+                    }
+                }
+            }
+        }
+    }
+    if (next_leaf != nl) {
+        hg::set_error("leaf count %lld does not match n_leaves %lld", (long long)next_leaf, (long long)nl);
+        return HG_EFORMAT;
+    }
+    for (int64_t i = 1; i < n; i++)
+        if (parent[i] < 0) {
+            hg::set_error("node %lld is unreachable", (long long)i);
+            return HG_EFORMAT;
+        }
+    std::vector<int64_t> leaf_node((size_t)nl);
+    for (int64_t i = 0; i < n; i++)
+        if (D.node_leaf[i] >= 0) leaf_node[D.node_leaf[i]] = i;
+    for (int64_t j = 0; j < nl; j++)
+        if (!std::isfinite(D.leaf_rho[j])) {
+            hg::set_error("leaf %lld has a non-finite density", (long long)j);
+            return HG_EFORMAT;
+        }
+    // neighbor lists: adjacency, positive overlap, tiling, order
+    if (D.nbr_off[0] != 0) { hg::set_error("nbr_off[0] must be 0"); return HG_EFORMAT; }
+    const double *dlo = D.node_lo, *dhi = D.node_hi;
+    for (int64_t i = 0; i < nl; i++) {
+        const double *lo = D.node_lo + 3 * leaf_node[i], *hi = D.node_hi + 3 * leaf_node[i];
+        for (int w = 0; w < 6; w++) {
+            const int a = w >> 1, s = w & 1;
+            const int64_t b0 = D.nbr_off[6 * i + w], b1 = D.nbr_off[6 * i + w + 1];
+            if (b1 < b0) { hg::set_error("nbr_off not monotone at leaf %lld", (long long)i); return HG_EFORMAT; }
+            const double plane = s ? hi[a] : lo[a];
+            const bool boundary = s ? (plane == dhi[a]) : (plane == dlo[a]);
+            if (boundary != (b1 == b0)) {
+                hg::set_error("leaf %lld wall %d: list must be empty exactly on the domain boundary", (long long)i, w);
+                return HG_EFORMAT;
+            }
+            const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+            const double wall_area = (hi[t1] - lo[t1]) * (hi[t2] - lo[t2]);
+            double sum = 0.0, prev = INFINITY;
+            for (int64_t e = b0; e < b1; e++) {
+                const int32_t j = D.nbr_id[e];
+                if (j < 0 || j >= nl) { hg::set_error("neighbor id %d out of range", j); return HG_EFORMAT; }
+                const double *jlo = D.node_lo + 3 * leaf_node[j], *jhi = D.node_hi + 3 * leaf_node[j];
+                if ((s ? jlo[a] : jhi[a]) != plane) {
+                    hg::set_error("leaf %lld wall %d: neighbor %d is not adjacent", (long long)i, w, j);
+                    return HG_EFORMAT;
+                }
+                double o1 = std::min(hi[t1], jhi[t1]) - std::max(lo[t1], jlo[t1]);
+                double o2 = std::min(hi[t2], jhi[t2]) - std::max(lo[t2], jlo[t2]);
+                if (!(o1 > 0.0 && o2 > 0.0)) {
+                    hg::set_error("leaf %lld wall %d: neighbor %d has no overlap", (long long)i, w, j);
+                    return HG_EFORMAT;
+                }
+                double area = o1 * o2;
+                if (area > prev * (1.0 + 1e-12)) {
+                    hg::set_error("leaf %lld wall %d: list not sorted by decreasing overlap", (long long)i, w);
+                    return HG_EFORMAT;
+                }
+                prev = area;
+                sum += area;
+            }
+            if (b1 > b0 && std::fabs(sum - wall_area) > 1e-9 * wall_area) {
+                hg::set_error("leaf %lld wall %d: neighbors do not tile the wall", (long long)i, w);
+                return HG_EFORMAT;
+            }
+        }
+    }
+    return HG_OK;
+}
+
+}  // namespace
+
+extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_flag, hg_grid **out) {
+    if (!desc || !out) { hg::set_error("hg_load_grid: null argument"); return HG_EINVAL; }
+    *out = nullptr;
+    const hg_grid_desc D = *desc;
+    if ((D.kind != HG_OCTREE && D.kind != HG_KDTREE) || D.n_nodes < 1 || D.n_leaves < 1 || !D.node_lo ||
+        !D.node_hi || !D.child_first || !D.node_leaf || !D.leaf_rho || !D.nbr_off || !D.nbr_id) {
+        hg::set_error("hg_load_grid: incomplete description");
+        return HG_EINVAL;
+    }
+    if (D.n_leaves > INT32_MAX || D.n_nodes > INT32_MAX) {
+        hg::set_error("hg_load_grid: ids must fit in int32");
+        return HG_EINVAL;
+    }
+    if (validate_flag) {
+        hg_status st = validate(D);
+        if (st != HG_OK) return st;
+    }
+    const int64_t n = D.n_nodes, nl = D.n_leaves;
+    std::unique_ptr<hg_grid> g(new hg_grid());
+    try {
+        // node depths for the descent limit
+        std::vector<int32_t> depth((size_t)n, 0);
+        int32_t max_depth = 0;
+        const int nch = (D.kind == HG_OCTREE) ? 8 : 2;
+        for (int64_t i = 0; i < n; i++)
+            if (D.child_first[i] >= 0)
+                for (int j = 0; j < nch; j++) {
+                    depth[D.child_first[i] + j] = depth[i] + 1;
+                    max_depth = std::max(max_depth, depth[i] + 1);
+                }
+        // descent nodes
+        std::vector<unsigned char> nodes;
+        if (D.kind == HG_KDTREE) {
+            nodes.resize((size_t)n * sizeof(hg::KdNode));
+            hg::KdNode *K = reinterpret_cast<hg::KdNode *>(nodes.data());
+            for (int64_t i = 0; i < n; i++) {
+                const int32_t c = D.child_first[i];
+                K[i].child = c;
+                if (c < 0) {
+                    K[i].split = 0.0;
+                    K[i].info = D.node_leaf[i];
+                } else {
+                    int ax = 0;
+                    while (ax < 2 && D.node_hi[3 * (int64_t)c + ax] == D.node_hi[3 * i + ax]) ax++;
+                    K[i].split = D.node_hi[3 * (int64_t)c + ax];
+                    K[i].info = ax;
+                }
+            }
+        } else {
+            nodes.resize((size_t)n * sizeof(hg::OctNode));
+            hg::OctNode *O = reinterpret_cast<hg::OctNode *>(nodes.data());
+            for (int64_t i = 0; i < n; i++) {
+                const int32_t c = D.child_first[i];
+                O[i].child = c;
+                O[i].leaf = D.node_leaf[i];
+                for (int a = 0; a < 3; a++) O[i].s[a] = (c < 0) ? 0.0 : D.node_hi[3 * (int64_t)c + a];
+            }
+        }
+        // leaf records and neighbor-list tails
+        std::vector<int64_t> leaf_node((size_t)nl);
+        for (int64_t i = 0; i < n; i++)
+            if (D.node_leaf[i] >= 0) leaf_node[D.node_leaf[i]] = i;
+        std::vector<hg::LeafRec> rec((size_t)nl);
+        std::vector<int32_t> tail;
+        int64_t long_walls = 0;
+        const double *dhi = D.node_hi;
+        for (int64_t i = 0; i < nl; i++) {
+            hg::LeafRec &R = rec[i];
+            std::memset(&R, 0, sizeof(R));
+            const int64_t nd = leaf_node[i];
+            for (int a = 0; a < 3; a++) {
+                R.lo[a] = D.node_lo[3 * nd + a];
+                R.hi[a] = D.node_hi[3 * nd + a];
+                if (R.hi[a] == dhi[a]) R.flags |= (uint8_t)(1u << a);
+            }
+            R.rho = D.leaf_rho[i];
+            R.rho32 = (float)D.leaf_rho[i];
+            if (tail.size() > UINT32_MAX) {
+                hg::set_error("hg_load_grid: neighbor tails exceed 2^32 entries");
+                return HG_EOVERFLOW;
+            }
+            R.nbr_base = (uint32_t)tail.size();
+            for (int w = 0; w < 6; w++) {
+                const int64_t b0 = D.nbr_off[6 * i + w], b1 = D.nbr_off[6 * i + w + 1];
+                const int64_t cnt = b1 - b0;
+                R.first[w] = cnt > 0 ? D.nbr_id[b0] : -1;
+                R.cnt[w] = (uint8_t)std::min<int64_t>(cnt, 255);
+                if (cnt >= 2 && cnt <= kScanLimit) {
+                    for (int64_t e = b0 + 1; e < b1; e++) tail.push_back(D.nbr_id[e]);
+                } else if (cnt > kScanLimit) {
+                    long_walls++;
+                }
+            }
+        }
+        if (tail.empty()) tail.push_back(-1);
+
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "hg_load_grid: no CUDA device");
+        g->device = dev;
+        auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+            cudaError_t r = cudaMalloc(dst, bytes);
+            if (r != cudaSuccess) return r;
+            return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        };
+        if ((e = upload(&g->d_rec, rec.data(), rec.size() * sizeof(hg::LeafRec))) != cudaSuccess ||
+            (e = upload(&g->d_tail, tail.data(), tail.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload(&g->d_nodes, nodes.data(), nodes.size())) != cudaSuccess) {
+            hg_status st = cuda_fail(e, "hg_load_grid: upload");
+            hg_free_grid(g.release());
+            return st;
+        }
+        hg::DevGrid &G = g->d;
+        G.rec = static_cast<const hg::LeafRec *>(g->d_rec);
+        G.tail = static_cast<const int32_t *>(g->d_tail);
+        G.nodes = g->d_nodes;
+        for (int a = 0; a < 3; a++) {
+            G.dlo[a] = D.node_lo[a];
+            G.dhi[a] = D.node_hi[a];
+        }
+        G.n_leaves = nl;
+        G.n_nodes = n;
+        G.kind = D.kind;
+        G.max_depth = max_depth;
+        G.scan_limit = kScanLimit;
+        hg_grid_info &I = g->info;
+        I.kind = D.kind;
+        I.max_depth = max_depth;
+        I.n_nodes = n;
+        I.n_leaves = nl;
+        I.n_tail = (int64_t)tail.size();
+        I.device_bytes = (int64_t)(rec.size() * sizeof(hg::LeafRec) + tail.size() * 4 + nodes.size());
+        I.long_walls = long_walls;
+        for (int a = 0; a < 3; a++) {
+            I.lo[a] = G.dlo[a];
+            I.hi[a] = G.dhi[a];
+        }
+    } catch (const std::bad_alloc &) {
+        hg::set_error("hg_load_grid: out of host memory");
+        return HG_ENOMEM;
+    }
+    *out = g.release();
+    return HG_OK;
+}
+
+extern "C" void hg_free_grid(hg_grid *g) {
+    if (!g) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != g->device) cudaSetDevice(g->device);
+    if (g->d_rec) cudaFree(g->d_rec);
+    if (g->d_tail) cudaFree(g->d_tail);
+    if (g->d_nodes) cudaFree(g->d_nodes);
+    if (cur != g->device) cudaSetDevice(cur);
+    delete g;
+}
+
+extern "C" hg_status hg_grid_get_info(const hg_grid *g, hg_grid_info *out) {
+    if (!g || !out) { hg::set_error("hg_grid_get_info: null argument"); return HG_EINVAL; }
+    *out = g->info;
+    return HG_OK;
+}

@@ -1,0 +1,585 @@
+// Path-calculation kernels and their C entry points: optical depth and
+// crossing counts, segment emission, adjoint scatter, density sampling,
+// plus the small scan / reduction kernels the path needs.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "hg_internal.h"
+#include "walk.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hg {
+
+enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2 };
+
+struct TraceArgs {
+    DevGrid G;
+    int64_t n;
+    const double *o;
+    const double *d;
+    const double *smax;
+    double kappa;
+    void *tau;
+    int32_t *ncross;
+    uint8_t *status;
+    const int64_t *seg_off;
+    int32_t *seg_cell;
+    void *seg_ds;
+    int64_t seg_cap;
+    const float *w;
+    void *grad;
+    const double *rho_ext;  // densities replacing the grid's own (MODE_TAU), or NULL
+    int64_t max_steps;
+    unsigned long long *counter;
+    int n_smem;
+    int dyn;
+};
+
+// Stage the first n nodes of the (breadth-first) node list in shared memory.
+__device__ __forceinline__ void stage_nodes(const void *nodes, int bytes, unsigned char *smem) {
+    const int4 *src = reinterpret_cast<const int4 *>(nodes);
+    int4 *dst = reinterpret_cast<int4 *>(smem);
+    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+}
+
+// One persistent loop per thread: a lane whose ray has ended takes the next
+// ray (static stride, or a warp-aggregated atomic on a global counter) and
+// every iteration advances each lane by one crossing, so lanes never wait
+// for the longest path in their warp.
+//   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
+//   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
+template <int KIND, int MODE, int PREC>
+__global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevGrid &G = A.G;
+    const int node_bytes = (KIND == HG_KDTREE) ? 16 : 32;
+    stage_nodes(G.nodes, A.n_smem * node_bytes, smem);
+
+    int64_t next = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t ray = -1;
+    RayState S;
+    Leaf L;
+    double acc = 0.0;     // FP64 sum of rho*ds
+    float acc32 = 0.0f;   // FP32 Kahan sum
+    float comp32 = 0.0f;  // Kahan compensation
+    float kr32 = 0.0f;    // (float)kappa * rho32 of the current leaf
+    int32_t nc = 0;
+    int64_t seg_base = 0;
+    double wk = 0.0;  // kappa * w for the adjoint
+    uint32_t st = 0;
+    const float kappa32 = (float)A.kappa;
+
+    for (;;) {
+        if (ray < 0) {
+            if (A.dyn) {
+                cg::coalesced_group g = cg::coalesced_threads();
+                unsigned long long base = 0;
+                if (g.thread_rank() == 0) base = atomicAdd(A.counter, (unsigned long long)g.size());
+                base = g.shfl(base, 0);
+                ray = (int64_t)(base + g.thread_rank());
+            } else {
+                ray = next;
+                next += stride;
+            }
+            if (ray >= A.n) break;
+            acc = 0.0;
+            acc32 = 0.0f;
+            comp32 = 0.0f;
+            nc = 0;
+            if (MODE == MODE_FILL) seg_base = A.seg_off[ray];
+            if (MODE == MODE_ADJ) wk = A.kappa * (double)A.w[ray];
+            const int r0 = ray_init<KIND>(G, smem, A.n_smem, A.o, A.d, A.smax, ray, S, L, &st);
+            if (r0 == WALK_END) goto finish;
+        }
+        {
+            double ds;
+            int ax;
+            double tex;
+            const int r1 = ray_exit(A.max_steps, S, L, &ds, &ax, &tex, &st);
+            if (ds != 0.0) {
+                if (MODE == MODE_TAU) {
+                    if (PREC == HG_FP64) {
+                        const double rho = A.rho_ext ? __ldg(A.rho_ext + S.cur) : L.rho;
+                        acc = acc + rho * ds;
+                    } else {
+                        const float rho32 = A.rho_ext ? __double2float_rn(__ldg(A.rho_ext + S.cur)) : L.rho32;
+                        kr32 = __fmul_rn(kappa32, rho32);
+                        const float y = __fsub_rn(__fmul_rn(kr32, __double2float_rn(ds)), comp32);
+                        const float t = __fadd_rn(acc32, y);
+                        comp32 = __fsub_rn(__fsub_rn(t, acc32), y);
+                        acc32 = t;
+                    }
+                } else if (MODE == MODE_FILL) {
+                    const int64_t idx = seg_base + nc;
+                    if (idx >= A.seg_cap) {
+                        st |= HG_RAY_OVERFLOW;
+                        goto finish;
+                    }
+                    A.seg_cell[idx] = S.cur;
+                    if (PREC == HG_FP64)
+                        static_cast<double *>(A.seg_ds)[idx] = ds;
+                    else
+                        static_cast<float *>(A.seg_ds)[idx] = __double2float_rn(ds);
+                } else {
+                    const double v = wk * ds;
+                    if (PREC == 0)
+                        atomicAdd(static_cast<double *>(A.grad) + S.cur, v);
+                    else
+                        atomicAdd(static_cast<float *>(A.grad) + S.cur, __double2float_rn(v));
+                }
+                nc++;
+            }
+            if (r1 == WALK_END) goto finish;
+            if (ray_advance<KIND>(G, smem, A.n_smem, S, L, ax, tex, &st) == WALK_END) goto finish;
+            continue;
+        }
+    finish:
+        if (MODE == MODE_TAU) {
+            if (PREC == HG_FP64)
+                static_cast<double *>(A.tau)[ray] = A.kappa * acc;
+            else
+                static_cast<float *>(A.tau)[ray] = acc32;
+            A.ncross[ray] = nc;
+            if (A.status) A.status[ray] = (uint8_t)st;
+        } else if (MODE == MODE_FILL) {
+            if (A.status && st) A.status[ray] |= (uint8_t)st;
+        } else {
+            if (A.status) A.status[ray] = (uint8_t)st;
+        }
+        ray = -1;
+    }
+}
+
+// ------------------------------------------------------------------ launch plumbing
+
+typedef void (*KernelFn)(const TraceArgs);
+
+KernelFn pick_kernel(int kind, int mode, int prec) {
+#define HG_K(K, M, P) &trace_kernel<K, M, P>
+    static const KernelFn table[2][3][2] = {
+        {{HG_K(0, 0, 0), HG_K(0, 0, 1)}, {HG_K(0, 1, 0), HG_K(0, 1, 1)}, {HG_K(0, 2, 0), HG_K(0, 2, 1)}},
+        {{HG_K(1, 0, 0), HG_K(1, 0, 1)}, {HG_K(1, 1, 0), HG_K(1, 1, 1)}, {HG_K(1, 2, 0), HG_K(1, 2, 1)}}};
+#undef HG_K
+    return table[kind][mode][prec];
+}
+
+hg_status cuda_err(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HG_ENOMEM : HG_ECUDA;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// Default launch shape: 256 threads, the top 2048 k-d nodes (32 KB) or
+// 1024 octree nodes (32 KB) in shared memory, persistent dynamic schedule.
+hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precision, int &block, int &smem_nodes,
+                       int &schedule, int64_t &max_steps) {
+    precision = opts ? opts->precision : HG_FP64;
+    if (precision != HG_FP64 && precision != HG_FP32K) {
+        set_error("precision must be HG_FP64 or HG_FP32K");
+        return HG_EINVAL;
+    }
+    const TuneEntry &T = g->tuned[precision];
+    block = (opts && opts->block > 0) ? opts->block : (T.valid ? T.block : 256);
+    smem_nodes = (opts && opts->smem_nodes >= 0) ? opts->smem_nodes
+                                                  : (T.valid ? T.smem_nodes : (g->d.kind == HG_KDTREE ? 2048 : 1024));
+    schedule = (opts && opts->schedule > 0) ? opts->schedule : (T.valid ? T.schedule : 2);
+    max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 4 * g->d.n_leaves + 64;
+    if (block < 32 || block > 512 || block % 32) {
+        set_error("block must be a multiple of 32 in 32..512");
+        return HG_EINVAL;
+    }
+    if (schedule != 1 && schedule != 2) {
+        set_error("schedule must be 1 or 2");
+        return HG_EINVAL;
+    }
+    smem_nodes = (int)std::min<int64_t>(smem_nodes, g->d.n_nodes);
+    const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
+    if ((int64_t)smem_nodes * node_bytes > 200 * 1024) {
+        set_error("smem_nodes exceeds 200 KB of shared memory");
+        return HG_EINVAL;
+    }
+    return HG_OK;
+}
+
+hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int block, int smem_nodes, int schedule,
+                       cudaStream_t stream) {
+    if (A.n == 0) return HG_OK;
+    KernelFn k = pick_kernel(g->d.kind, mode, prec);
+    const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
+    const size_t smem = (size_t)smem_nodes * node_bytes;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int kd = 0; kd < 2; kd++)
+            for (int m = 0; m < 3; m++)
+                for (int p = 0; p < 2; p++)
+                    cudaFuncSetAttribute(pick_kernel(kd, m, p), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    });
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
+    if (e != cudaSuccess) return cuda_err(e, "occupancy query");
+    if (per_sm < 1) {
+        set_error("launch shape does not fit on an SM (block %d, %zu B shared)", block, smem);
+        return HG_EINVAL;
+    }
+    int64_t blocks = (int64_t)per_sm * sm_count();
+    const int64_t need = (A.n + block - 1) / block;
+    if (blocks > need) blocks = need;
+    A.n_smem = smem_nodes;
+    A.dyn = (schedule == 2);
+    unsigned long long *ctr = nullptr;
+    if (A.dyn) {
+        e = cudaMallocAsync((void **)&ctr, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return cuda_err(e, "scratch counter");
+        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(ctr, stream);
+            return cuda_err(e, "scratch counter");
+        }
+        A.counter = ctr;
+    }
+    k<<<(unsigned)blocks, block, smem, stream>>>(A);
+    e = cudaGetLastError();
+    note_launches(1);
+    if (ctr) cudaFreeAsync(ctr, stream);
+    if (e != cudaSuccess) return cuda_err(e, "trace launch");
+    return HG_OK;
+}
+
+hg_status check_rays(const hg_grid *g, int64_t n, const double *o, const double *d) {
+    if (!g) {
+        set_error("null grid");
+        return HG_EINVAL;
+    }
+    if (n < 0 || (n > 0 && (!o || !d))) {
+        set_error("bad ray arrays");
+        return HG_EINVAL;
+    }
+    return HG_OK;
+}
+
+// ------------------------------------------------------------------ density sampling
+
+template <int KIND>
+__global__ void sample_kernel(const DevGrid G, int64_t n, const double *__restrict__ pts, int32_t *cell,
+                              double *rho, int n_smem) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double p0 = pts[3 * i], p1 = pts[3 * i + 1], p2 = pts[3 * i + 2];
+        int32_t c = -1;
+        if (in_domain(G, p0, p1, p2, 0.0, 0.0, 0.0)) c = descend<KIND>(G, smem, n_smem, p0, p1, p2, 0.0, 0.0, 0.0);
+        if (cell) cell[i] = c;
+        rho[i] = (c >= 0) ? __ldg(&G.rec[c].rho) : 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ scan and reductions
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 8;  // per thread: one block covers 8192 counts
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *sh, int64_t *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const int64_t warp_prefix = wid ? sh[wid - 1] : 0;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+// Pass 1: sum of each tile of kScanBlock*kScanItems counts.
+__global__ void scan_tile_sums(int64_t n, const int32_t *__restrict__ c, int64_t *tile_sum) {
+    __shared__ int64_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems;
+    int64_t s = 0;
+    for (int j = 0; j < kScanItems; j++) {
+        const int64_t i = base + (int64_t)j * kScanBlock + threadIdx.x;
+        if (i < n) s += c[i];
+    }
+    int64_t tot;
+    block_excl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+// Pass 2: exclusive scan of the tile sums by one block (serial over chunks).
+__global__ void scan_tile_prefix(int64_t tiles, int64_t *tile_sum) {
+    __shared__ int64_t sh[32];
+    int64_t carry = 0;
+    for (int64_t b = 0; b < tiles; b += blockDim.x) {
+        const int64_t i = b + threadIdx.x;
+        const int64_t v = i < tiles ? tile_sum[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_excl_scan(v, sh, &tot);
+        if (i < tiles) tile_sum[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+// Pass 3: scan inside each tile, offset by the tile's prefix.
+__global__ void scan_tile_apply(int64_t n, const int32_t *__restrict__ c, const int64_t *tile_prefix,
+                                int64_t *out) {
+    __shared__ int64_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        const int64_t i = base + j;
+        v[j] = (i < n) ? c[i] : 0;
+        s += v[j];
+    }
+    int64_t tot;
+    int64_t run = tile_prefix[blockIdx.x] + block_excl_scan(s, sh, &tot);
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        const int64_t i = base + j;
+        if (i < n) out[i] = run;
+        run += v[j];
+    }
+    if (base < n && n <= base + kScanItems) out[n] = run;
+}
+
+__global__ void or_status_kernel(int64_t n, const uint8_t *__restrict__ s, uint32_t *out) {
+    uint32_t v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v |= s[i];
+    v = __reduce_or_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicOr(out, v);
+}
+
+__global__ void sum_i32_kernel(int64_t n, const int32_t *__restrict__ x, unsigned long long *out) {
+    long long v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v += x[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+
+}  // namespace hg
+
+using namespace hg;
+
+extern "C" hg_status hg_trace_rays(const hg_grid *g, int64_t n, const double *o, const double *d,
+                                   const double *s_max, double kappa, const hg_trace_opts *opts, void *tau,
+                                   int32_t *ncross, uint8_t *ray_status, hg_stream stream) {
+    hg_status st = check_rays(g, n, o, d);
+    if (st != HG_OK) return st;
+    if (n > 0 && (!tau || !ncross)) {
+        set_error("hg_trace_rays: tau and ncross are required");
+        return HG_EINVAL;
+    }
+    int prec, block, smem_nodes, schedule;
+    int64_t max_steps;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    TraceArgs A{};
+    A.G = g->d;
+    A.n = n;
+    A.o = o;
+    A.d = d;
+    A.smax = s_max;
+    A.kappa = kappa;
+    A.tau = tau;
+    A.ncross = ncross;
+    A.status = ray_status;
+    A.max_steps = max_steps;
+    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double *o, const double *d,
+                                       const double *s_max, double kappa, const double *rho,
+                                       const hg_trace_opts *opts, void *tau, int32_t *ncross, uint8_t *ray_status,
+                                       hg_stream stream) {
+    hg_status st = check_rays(g, n, o, d);
+    if (st != HG_OK) return st;
+    if (n > 0 && (!tau || !ncross || !rho)) {
+        set_error("hg_trace_rays_rho: rho, tau and ncross are required");
+        return HG_EINVAL;
+    }
+    int prec, block, smem_nodes, schedule;
+    int64_t max_steps;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    TraceArgs A{};
+    A.G = g->d;
+    A.n = n;
+    A.o = o;
+    A.d = d;
+    A.smax = s_max;
+    A.kappa = kappa;
+    A.rho_ext = rho;
+    A.tau = tau;
+    A.ncross = ncross;
+    A.status = ray_status;
+    A.max_steps = max_steps;
+    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o, const double *d,
+                                   const double *s_max, const hg_trace_opts *opts, const int64_t *seg_off,
+                                   int32_t *seg_cell, void *seg_ds, int64_t seg_capacity, uint8_t *ray_status,
+                                   hg_stream stream) {
+    hg_status st = check_rays(g, n, o, d);
+    if (st != HG_OK) return st;
+    if (n > 0 && (!seg_off || (seg_capacity > 0 && (!seg_cell || !seg_ds)) || seg_capacity < 0)) {
+        set_error("hg_trace_fill: bad segment arrays");
+        return HG_EINVAL;
+    }
+    int prec, block, smem_nodes, schedule;
+    int64_t max_steps;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    TraceArgs A{};
+    A.G = g->d;
+    A.n = n;
+    A.o = o;
+    A.d = d;
+    A.smax = s_max;
+    A.seg_off = seg_off;
+    A.seg_cell = seg_cell;
+    A.seg_ds = seg_ds;
+    A.seg_cap = seg_capacity;
+    A.status = ray_status;
+    A.max_steps = max_steps;
+    return launch_trace(g, MODE_FILL, prec, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *o, const double *d,
+                                     const double *s_max, double kappa, const float *w, int32_t grad_precision,
+                                     void *grad_rho, const hg_trace_opts *opts, hg_stream stream) {
+    hg_status st = check_rays(g, n, o, d);
+    if (st != HG_OK) return st;
+    if (n > 0 && (!w || !grad_rho)) {
+        set_error("hg_tau_gradient: w and grad_rho are required");
+        return HG_EINVAL;
+    }
+    if (grad_precision != 0 && grad_precision != 1) {
+        set_error("hg_tau_gradient: grad_precision must be 0 (f64) or 1 (f32)");
+        return HG_EINVAL;
+    }
+    int prec, block, smem_nodes, schedule;
+    int64_t max_steps;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    TraceArgs A{};
+    A.G = g->d;
+    A.n = n;
+    A.o = o;
+    A.d = d;
+    A.smax = s_max;
+    A.kappa = kappa;
+    A.w = w;
+    A.grad = grad_rho;
+    A.max_steps = max_steps;
+    return launch_trace(g, MODE_ADJ, grad_precision, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_sample_density(const hg_grid *g, int64_t n, const double *pts, int32_t *cell, double *rho,
+                                       hg_stream stream) {
+    if (!g || n < 0 || (n > 0 && (!pts || !rho))) {
+        set_error("hg_sample_density: bad arguments");
+        return HG_EINVAL;
+    }
+    if (n == 0) return HG_OK;
+    const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
+    const int n_smem = (int)std::min<int64_t>(g->d.n_nodes, (32 * 1024) / node_bytes);
+    const size_t smem = (size_t)n_smem * node_bytes;
+    const int block = 256;
+    int64_t blocks = std::min<int64_t>((n + block - 1) / block, (int64_t)sm_count() * 8);
+    if (g->d.kind == HG_KDTREE)
+        sample_kernel<HG_KDTREE><<<(unsigned)blocks, block, smem, (cudaStream_t)stream>>>(g->d, n, pts, cell, rho,
+                                                                                         n_smem);
+    else
+        sample_kernel<HG_OCTREE><<<(unsigned)blocks, block, smem, (cudaStream_t)stream>>>(g->d, n, pts, cell, rho,
+                                                                                         n_smem);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "sample launch");
+}
+
+extern "C" hg_status hg_scan_offsets(int64_t n, const int32_t *count, int64_t *seg_off, hg_stream stream) {
+    if (n < 0 || !seg_off || (n > 0 && !count)) {
+        set_error("hg_scan_offsets: bad arguments");
+        return HG_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(seg_off, 0, sizeof(int64_t), s);
+        return e == cudaSuccess ? HG_OK : cuda_err(e, "scan");
+    }
+    const int64_t tile = (int64_t)kScanBlock * kScanItems;
+    const int64_t tiles = (n + tile - 1) / tile;
+    int64_t *sums = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&sums, (size_t)tiles * sizeof(int64_t), s);
+    if (e != cudaSuccess) return cuda_err(e, "scan scratch");
+    scan_tile_sums<<<(unsigned)tiles, kScanBlock, 0, s>>>(n, count, sums);
+    scan_tile_prefix<<<1, kScanBlock, 0, s>>>(tiles, sums);
+    scan_tile_apply<<<(unsigned)tiles, kScanBlock, 0, s>>>(n, count, sums, seg_off);
+    note_launches(3);
+    e = cudaGetLastError();
+    cudaFreeAsync(sums, s);
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "scan launch");
+}
+
+extern "C" hg_status hg_reduce_status(int64_t n, const uint8_t *ray_status, uint32_t *out_bits, hg_stream stream) {
+    if (n < 0 || !out_bits || (n > 0 && !ray_status)) {
+        set_error("hg_reduce_status: bad arguments");
+        return HG_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess && n > 0) {
+        int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 4);
+        or_status_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, ray_status, out_bits);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "status reduce");
+}
+
+extern "C" hg_status hg_sum_i32(int64_t n, const int32_t *x, int64_t *out, hg_stream stream) {
+    if (n < 0 || !out || (n > 0 && !x)) {
+        set_error("hg_sum_i32: bad arguments");
+        return HG_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    if (e == cudaSuccess && n > 0) {
+        int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 4);
+        sum_i32_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, x, reinterpret_cast<unsigned long long *>(out));
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "sum");
+}

@@ -1,0 +1,176 @@
+"""Host-side checks of the library (no GPU): exported C ABI, tree builder
+against the oracle's node list, neighbor-list invariants, and rejection of
+malformed grid descriptions by hg_load_grid's validation."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+hg = pytest.importorskip("paper_1311_0705_gb300")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+    hdr = open(os.path.join(ROOT, "include", "hgrt.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(hg_[a-z0-9_]+)\s*\(", hdr))
+    assert len(names) >= 25
+    lib = ctypes.CDLL(hg.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding wraps every declared function
+    assert names <= set(hg.EXPORTED), sorted(names - set(hg.EXPORTED))
+
+
+def test_status_strings_and_bits():
+    assert hg._lib.hg_status_str(0) == b"ok"
+    assert hg.status_from_bits(0) == 0
+    assert hg.status_from_bits(hg.RAY_LOST | hg.RAY_STEPLIMIT) == 6
+    assert hg.status_from_bits(hg.RAY_STEPLIMIT) == 5
+
+
+def _same_tree(H, T):
+    assert H.n_nodes == T.n_nodes and H.n_leaves == T.n_leaves
+    np.testing.assert_array_equal(H.node_lo, T.lo)
+    np.testing.assert_array_equal(H.node_hi, T.hi)
+    np.testing.assert_array_equal(H.child_first, T.child)
+    np.testing.assert_array_equal(H.node_leaf, T.leaf)
+    np.testing.assert_array_equal(H.leaf_rho, T.leaf_rho)
+    np.testing.assert_array_equal(H.mass, T.mass)
+    np.testing.assert_array_equal(H.q, T.q)
+    np.testing.assert_array_equal(H.tau, T.taun)
+    np.testing.assert_array_equal(H.level, T.lvl)
+    np.testing.assert_array_equal(H.index, T.idx)
+
+
+CASES = [
+    ("disk-oct", lambda: synth.make_disk(), dict(kind=0, delta_max=1e-4, max_level=6)),
+    ("disk-kd", lambda: synth.make_disk(), dict(kind=1, delta_max=5e-5, max_level=6)),
+    ("torus-kd-all", lambda: synth.make_torus(11, n_clumps=60), dict(kind=1, delta_max=1e-3, use_tau=True,
+                                                                     tau_max=2.0, use_q=True, q_max=0.9,
+                                                                     max_level=5)),
+    ("torus-oct-q", lambda: synth.make_torus(12, n_clumps=30), dict(kind=0, delta_max=1e-2, use_q=True,
+                                                                    q_max=0.99, max_level=4)),
+    ("dyadic-oct", lambda: synth.make_dyadic(3, level=2), dict(kind=0, delta_max=1e-3, max_level=4)),
+    ("const-tau", lambda: synth.make_const(2.0), dict(kind=1, use_delta=False, use_tau=True, tau_max=0.9,
+                                                      max_level=6)),
+]
+
+
+@pytest.mark.parametrize("name,mk,kw", CASES, ids=[c[0] for c in CASES])
+def test_builder_matches_oracle_bit_exact(name, mk, kw):
+    model = mk()
+    bp = synth.BuildParams(seed=synth.BASE_SEED + 17, **kw)
+    H = hg.build_grid(model, bp, threads=4)
+    T = oracle.build_tree(model, bp)
+    _same_tree(H, T)
+
+
+def test_builder_independent_of_thread_count():
+    model = synth.make_torus(5, n_clumps=40)
+    bp = synth.BuildParams(kind=1, delta_max=2e-3, use_q=True, q_max=0.9, max_level=5)
+    a = hg.build_grid(model, bp, threads=1)
+    b = hg.build_grid(model, bp, threads=7)
+    np.testing.assert_array_equal(a.child_first, b.child_first)
+    np.testing.assert_array_equal(a.leaf_rho, b.leaf_rho)
+    np.testing.assert_array_equal(a.nbr_off, b.nbr_off)
+    np.testing.assert_array_equal(a.nbr_id, b.nbr_id)
+
+
+def _leaf_boxes(H):
+    ln = H.leaf_node
+    return H.node_lo[ln], H.node_hi[ln]
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_neighbor_lists_tile_walls_and_are_symmetric(kind):
+    model = synth.make_disk()
+    H = hg.build_grid(model, synth.BuildParams(kind=kind, delta_max=3e-4, max_level=6))
+    lo, hi = _leaf_boxes(H)
+    dlo, dhi = H.node_lo[0], H.node_hi[0]
+    pairs = set()
+    for i in range(H.n_leaves):
+        for w in range(6):
+            a, s = w // 2, w % 2
+            ids = H.nbr_id[H.nbr_off[6 * i + w]:H.nbr_off[6 * i + w + 1]]
+            plane = hi[i, a] if s else lo[i, a]
+            on_boundary = plane == (dhi[a] if s else dlo[a])
+            assert on_boundary == (ids.size == 0)
+            if ids.size == 0:
+                continue
+            t = [b for b in range(3) if b != a]
+            ov = np.ones(ids.size)
+            for b in t:
+                ov *= np.minimum(hi[i, b], hi[ids, b]) - np.maximum(lo[i, b], lo[ids, b])
+            assert (ov > 0).all()
+            # adjacent across the wall, sorted by decreasing overlap, tiling the wall
+            np.testing.assert_array_equal(lo[ids, a] if s else hi[ids, a], plane)
+            assert (np.diff(ov) <= 0).all()
+            area = (hi[i, t[0]] - lo[i, t[0]]) * (hi[i, t[1]] - lo[i, t[1]])
+            assert ov.sum() == pytest.approx(area, rel=1e-15)
+            for j in ids:
+                pairs.add((i, w, int(j)))
+    for (i, w, j) in pairs:
+        assert (j, w ^ 1, i) in pairs
+
+
+def _desc(H):
+    d = H.desc()
+    return hg.GridDesc(d.kind, d.node_lo.copy(), d.node_hi.copy(), d.child_first.copy(), d.node_leaf.copy(),
+                       d.leaf_rho.copy(), d.nbr_off.copy(), d.nbr_id.copy())
+
+
+@pytest.fixture(scope="module")
+def small_host():
+    return hg.build_grid(synth.make_disk(), synth.BuildParams(kind=1, delta_max=2e-3, max_level=4))
+
+
+def _corrupt(desc, what):
+    if what == "cycle":
+        desc.child_first[desc.child_first > 0][0:1] = 0
+        idx = np.nonzero(desc.child_first > 0)[0][0]
+        desc.child_first[idx] = 0
+    elif what == "nbr_range":
+        desc.nbr_id[3] = 10 ** 8
+    elif what == "nbr_not_adjacent":
+        k = np.nonzero(np.diff(desc.nbr_off) > 0)[0][5]
+        e = desc.nbr_off[k]
+        desc.nbr_id[e] = (desc.nbr_id[e] + 7) % desc.leaf_rho.shape[0]
+    elif what == "not_tiling":
+        k = np.nonzero(np.diff(desc.nbr_off) >= 2)[0][0]
+        desc.nbr_off[k + 1] -= 1
+    elif what == "leaf_order":
+        lv = np.nonzero(desc.node_leaf >= 0)[0]
+        desc.node_leaf[lv[0]], desc.node_leaf[lv[1]] = desc.node_leaf[lv[1]], desc.node_leaf[lv[0]]
+    elif what == "child_box":
+        c = desc.child_first[0]
+        desc.node_hi[c, 0] += 1e-3
+    elif what == "nan_rho":
+        desc.leaf_rho[2] = np.nan
+    return desc
+
+
+@pytest.mark.parametrize("what", ["cycle", "nbr_range", "nbr_not_adjacent", "not_tiling", "leaf_order",
+                                  "child_box", "nan_rho"])
+def test_load_grid_rejects_corrupt_descriptions(small_host, what):
+    # validation runs on the host before any device work: no GPU needed
+    desc = _corrupt(_desc(small_host), what)
+    with pytest.raises(hg.HgError, match="grid description invalid"):
+        hg.load_grid(desc, validate=True)
+
+
+def test_builder_rejects_bad_parameters():
+    with pytest.raises(hg.HgError):
+        hg.build_grid(synth.make_disk(), synth.BuildParams(kind=0, max_level=25))
+    with pytest.raises(hg.HgError):
+        hg.build_grid(synth.make_disk(), synth.BuildParams(kind=0, n_ran=0))
+    bp = synth.BuildParams(kind=0, delta_max=-1.0, max_level=5)
+    bp.max_nodes = 100
+    with pytest.raises(hg.HgError, match="capacity"):
+        hg.build_grid(synth.make_const(), bp)

@@ -1,0 +1,382 @@
+"""GPU path calculation against the FP64 oracle, element by element.
+
+Cell sequences and crossing counts must match bit for bit; FP64 optical
+depths within 1e-6 relative (identical operation order makes them equal in
+practice); FP32-Kahan optical depths within 1e-5 relative of the oracle's
+FP64 value.  Every call goes through the C ABI (``paper_1311_0705_gb300``).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TAU_RTOL_FP64 = 1e-6
+TAU_RTOL_FP32K = 1e-5
+
+
+@pytest.fixture(scope="module")
+def hg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1311_0705_gb300 as m
+    return m
+
+
+def _cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _check_tau(got, ref, rtol):
+    got = np.asarray(got, np.float64)
+    err = np.abs(got - ref)
+    assert (err <= rtol * np.abs(ref) + 1e-300).all(), float((err / np.maximum(np.abs(ref), 1e-300)).max())
+
+
+def _compare(hg, grid, tree, o, k, smax=None, kappa=1.0, precision="fp64", max_steps=None, **opt):
+    ms = oracle.default_max_steps(tree.n_leaves) if max_steps is None else max_steps
+    ref = oracle.trace(tree, o, k, smax=smax, kappa=kappa, emit=True, max_steps=ms)
+    O, K = _cuda(o), _cuda(k)
+    S = None if smax is None else _cuda(smax)
+    out = hg.trace_emit(grid, O, K, S, kappa=kappa, precision=precision, max_steps=ms, **opt)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(_np(out["ncross"]), ref["ncross"])
+    np.testing.assert_array_equal(_np(out["status"]), ref["status"])
+    np.testing.assert_array_equal(_np(out["seg_off"]), ref["seg_off"])
+    np.testing.assert_array_equal(_np(out["seg_cell"]), ref["seg_cell"])
+    if precision == "fp64":
+        np.testing.assert_array_equal(_np(out["seg_ds"]), ref["seg_ds"])
+        _check_tau(_np(out["tau"]), ref["tau"], TAU_RTOL_FP64)
+    else:
+        np.testing.assert_array_equal(_np(out["seg_ds"]), ref["seg_ds"].astype(np.float32))
+        _check_tau(_np(out["tau"]), ref["tau"], TAU_RTOL_FP32K)
+    return ref, out
+
+
+# ----------------------------------------------------------------------------- grids
+
+@pytest.fixture(scope="module")
+def disk_grids(hg):
+    model, bp, n_rays, seed = synth.workload_disk_small()
+    out = {}
+    for kind in (synth.TREE_OCTREE, synth.TREE_KD):
+        bp.kind = kind
+        H = hg.build_grid(model, bp)
+        T = oracle.build_tree(model, bp)
+        np.testing.assert_array_equal(H.child_first, T.child)
+        np.testing.assert_array_equal(H.leaf_rho, T.leaf_rho)
+        out[kind] = (hg.load_grid(H), T, H)
+    o, k = synth.emission_rays(seed, n_rays)
+    return model, out, o, k
+
+
+SHAPES = [dict(), dict(schedule=1), dict(schedule=2, block=128, smem_nodes=0), dict(block=512, smem_nodes=64),
+          dict(schedule=1, block=64, smem_nodes=100000)]
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+@pytest.mark.parametrize("shape", SHAPES, ids=[str(s) for s in SHAPES])
+def test_small_disk_sequences_bit_exact(hg, disk_grids, kind, shape):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    _compare(hg, grid, tree, o, k, **shape)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_fp32k_sequence_and_tau_bound(hg, disk_grids, kind):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    _compare(hg, grid, tree, o, k, precision="fp32k")
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_path_ends_kappa_and_ragged_counts(hg, disk_grids, kind):
+    model, grids, _, _ = disk_grids
+    grid, tree, _ = grids[kind]
+    a, k, L = synth.endpoint_paths(77, 3001)
+    _compare(hg, grid, tree, a, k, smax=L, kappa=2.5)
+    _compare(hg, grid, tree, a, k, smax=L * 0.37, kappa=0.5, precision="fp32k")
+
+
+def test_outside_origins_misses_and_bad_inputs(hg, disk_grids):
+    model, grids, _, _ = disk_grids
+    grid, tree, _ = grids[0]
+    rng = np.random.default_rng(3)
+    o = rng.uniform(-3, 3, size=(2000, 3))
+    k = synth.isotropic_dirs(rng, 2000)
+    k[:10] = 0.0
+    k[10:20, 1] = np.nan
+    o[20:30, 0] = np.inf
+    k[30:40] = [[-0.0, 0.0, 1.0]] * 10
+    ref, _ = _compare(hg, grid, tree, o, k)
+    assert (ref["status"][:30] == oracle.RAY_BADINPUT).all()
+    assert (ref["ncross"] == 0).any() and (ref["ncross"] > 0).any()
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_degenerate_rays_on_uniform_grid(hg, kind):
+    model = synth.make_const(1.5)
+    bp = synth.BuildParams(kind=kind, delta_max=-1.0, max_level=3)
+    grid = hg.load_grid(hg.build_grid(model, bp))
+    tree = oracle.build_tree(model, bp)
+    o, k = synth.degenerate_rays(levels=3, n_random=2000, seed=kind + 5)
+    _compare(hg, grid, tree, o, k)
+    _compare(hg, grid, tree, o, k, smem_nodes=0, schedule=1)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_degenerate_rays_on_adaptive_grid(hg, kind):
+    # lattice-aligned rays through a refined grid exercise edge/corner exits and list scans
+    model = synth.make_torus(21, n_clumps=20)
+    bp = synth.BuildParams(kind=kind, delta_max=1e-3, use_q=True, q_max=0.9, max_level=5)
+    grid = hg.load_grid(hg.build_grid(model, bp))
+    tree = oracle.build_tree(model, bp)
+    o, k = synth.degenerate_rays(levels=5, n_random=3000, seed=kind + 9)
+    _compare(hg, grid, tree, o, k)
+    o2, k2 = synth.emission_rays(kind + 100, 5000)
+    _compare(hg, grid, tree, o2, k2)
+
+
+def test_step_limit_reported_like_oracle(hg, disk_grids):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[1]
+    ref, out = _compare(hg, grid, tree, o[:3000], k[:3000], max_steps=7)
+    assert (ref["status"] == oracle.RAY_STEPLIMIT).any()
+
+
+def test_empty_and_single_ray(hg, disk_grids):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[0]
+    tau, nc, st = hg.trace_rays(grid, _cuda(np.zeros((0, 3))), _cuda(np.zeros((0, 3))))
+    assert tau.numel() == 0
+    _compare(hg, grid, tree, o[:1], k[:1])
+
+
+# ----------------------------------------------------------------------------- scan, reductions
+
+@pytest.mark.parametrize("n", [0, 1, 5, 8191, 8192, 8193, 100003, 2_500_001])
+def test_scan_offsets(hg, n):
+    c = np.random.default_rng(n).integers(0, 200, size=n).astype(np.int32)
+    off = _np(hg.scan_offsets(_cuda(c, torch.int32)))
+    ref = np.zeros(n + 1, np.int64)
+    np.cumsum(c, out=ref[1:])
+    np.testing.assert_array_equal(off, ref)
+
+
+def test_status_and_sum_reductions(hg):
+    s = np.zeros(100000, np.uint8)
+    s[5] = 1
+    s[99999] = 4
+    assert int(_np(hg.reduce_status(_cuda(s, torch.uint8)))[0]) == 5
+    x = np.random.default_rng(1).integers(0, 1000, size=123457).astype(np.int32)
+    assert int(_np(hg.sum_i32(_cuda(x, torch.int32)))[0]) == int(x.sum())
+
+
+# ----------------------------------------------------------------------------- density and metrics
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_sample_density(hg, disk_grids, kind):
+    model, grids, _, _ = disk_grids
+    grid, tree, _ = grids[kind]
+    pts = synth.sample_points(31, 50000)
+    pts[:64] = np.array([[-1, -1, -1], [1, 1, 1], [0, 0, 0], [1, 0, 0]] * 16, np.float64)
+    pts[64:70] = [[2, 0, 0], [0, -1.5, 0], [0, 0, 1.0000001], [-1, -1, -1], [0.5, 0.25, -0.125], [1, 1, -1]]
+    ref_c, ref_r = oracle.sample_density(tree, pts)
+    c, r = hg.sample_density(grid, _cuda(pts))
+    np.testing.assert_array_equal(_np(c), ref_c)
+    np.testing.assert_array_equal(_np(r), ref_r)
+
+
+@pytest.mark.parametrize("mk", [lambda: synth.make_disk(), lambda: synth.make_torus(4, n_clumps=200),
+                                lambda: synth.make_dyadic(2, level=2), lambda: synth.make_const(3.0)],
+                         ids=["disk", "torus", "dyadic", "const"])
+def test_model_density_and_tau(hg, mk):
+    model = mk()
+    dm = hg.load_model(model)
+    pts = synth.sample_points(8, 20000)
+    rt = _np(hg.model_density(dm, _cuda(pts)))
+    np.testing.assert_allclose(rt, oracle.rho_true(model, pts), rtol=1e-14, atol=0)
+    a, k, L = synth.endpoint_paths(9, 500)
+    tt = _np(hg.model_tau(dm, _cuda(a), _cuda(k), _cuda(L), kappa=1.3))
+    np.testing.assert_allclose(tt, oracle.tau_true(model, a, k, L, kappa=1.3), rtol=1e-9, atol=1e-12)
+
+
+def test_delta_metrics_match_oracle(hg, disk_grids):
+    model, grids, _, _ = disk_grids
+    dm = hg.load_model(model)
+    for kind in (0, 1):
+        grid, tree, _ = grids[kind]
+        pts = synth.sample_points(12, 100000)
+        c, rg = hg.sample_density(grid, _cuda(pts))
+        rt = hg.model_density(dm, _cuda(pts))
+        st = _np(hg.diff_stats(rt, rg))
+        _, org = oracle.sample_density(tree, pts)
+        ort = oracle.rho_true(model, pts)
+        assert st[0] == 100000
+        assert st[2] == pytest.approx(oracle.population_std(ort - org), rel=1e-9)
+        a, k, L = synth.endpoint_paths(13, 3000)
+        tg, _, _ = hg.trace_rays(grid, _cuda(a), _cuda(k), _cuda(L))
+        tt = hg.model_tau(dm, _cuda(a), _cuda(k), _cuda(L))
+        st2 = _np(hg.diff_stats(tt, tg))
+        ot = oracle.tau_true(model, a, k, L)
+        og = oracle.trace(tree, a, k, smax=L)["tau"]
+        assert st2[2] == pytest.approx(oracle.population_std(ot - og), rel=1e-7)
+        assert st2[1] == pytest.approx((ot - og).mean(), rel=1e-6, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_adjoint_against_oracle_accumulation(hg, disk_grids, kind):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    w = synth.adjoint_weights(5, o.shape[0])
+    kappa = 1.7
+    ref = oracle.trace(tree, o, k, kappa=kappa, emit=True)
+    g64_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64),
+                             kappa)
+    g64 = _np(hg.tau_gradient(grid, _cuda(o), _cuda(k), _cuda(w, torch.float32), kappa=kappa, grad_precision="fp64"))
+    np.testing.assert_allclose(g64, g64_ref, rtol=1e-12, atol=1e-300)
+    g32 = _np(hg.tau_gradient(grid, _cuda(o), _cuda(k), _cuda(w, torch.float32), kappa=kappa,
+                              grad_precision="fp32")).astype(np.float64)
+    # per-cell bound: gamma_n * sum |terms| with n = contributions + 1 (cast of each term)
+    counts = np.bincount(ref["seg_cell"], minlength=tree.n_leaves).astype(np.float64)
+    u = 2.0 ** -24
+    gam = (counts + 1) * u / (1 - (counts + 1) * u)
+    assert (np.abs(g32 - g64_ref) <= gam * np.abs(g64_ref) + 1e-30).all()
+
+
+def test_taufn_autograd_and_finite_differences(hg, disk_grids):
+    model, grids, o, k = disk_grids
+    grid, tree, H = grids[1]
+    O, K = _cuda(o[:2000]), _cuda(k[:2000])
+    rho = torch.tensor(H.leaf_rho, dtype=torch.float64, device="cuda", requires_grad=True)
+    w = torch.tensor(synth.adjoint_weights(6, 2000), device="cuda").to(torch.float64)
+    tau = hg.TauFn.apply(rho, grid, O, K, None, 1.1)
+    tau_plain, _, _ = hg.trace_rays(grid, O, K, kappa=1.1)
+    np.testing.assert_array_equal(_np(tau), _np(tau_plain))
+    (w * tau).sum().backward()
+    g = _np(rho.grad)
+    rng = np.random.default_rng(0)
+    hit = np.nonzero(g)[0]
+    cells = np.concatenate([rng.choice(hit, 50, replace=False), rng.integers(0, grid.n_leaves, 50)])
+    base = rho.detach().clone()
+    for c in cells:
+        h = 1e-3 * max(1.0, float(base[c]))
+        vals = []
+        for sgn in (1, -1):
+            r = base.clone()
+            r[c] += sgn * h
+            t, _ = hg.trace_rays_rho(grid, O, K, r, kappa=1.1)
+            vals.append(float((w * t).sum()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert fd == pytest.approx(g[c], rel=1e-6, abs=1e-10)
+
+
+# ----------------------------------------------------------------------------- batching and tuning
+
+def test_batch_matches_single_grid_launches(hg):
+    specs = synth.batch_specs(n_grids=6, rays_lo=1e3, rays_hi=2e4, leaves_lo=2e3, leaves_hi=3e4)
+    grids, os_, ks, begins = [], [], [], [0]
+    for i, sp in enumerate(specs):
+        bp = synth.BuildParams(kind=sp["kind"], delta_max=1.0 / sp["target_leaves"], max_level=7, seed=sp["seed"])
+        grids.append(hg.load_grid(hg.build_grid(sp["model"], bp)))
+        o, k = synth.emission_rays(sp["seed"], sp["n_rays"])
+        os_.append(o)
+        ks.append(k)
+        begins.append(begins[-1] + sp["n_rays"])
+    O = _cuda(np.concatenate(os_))
+    K = _cuda(np.concatenate(ks))
+    b = hg.Batch(grids, begins)
+    for prec in ("fp64", "fp32k"):
+        tau, nc, st = b.trace(O, K, kappa=1.4, precision=prec)
+        for i, g in enumerate(grids):
+            s = slice(begins[i], begins[i + 1])
+            t1, n1, s1 = hg.trace_rays(g, O[s].contiguous(), K[s].contiguous(), kappa=1.4, precision=prec)
+            np.testing.assert_array_equal(_np(tau[s]), _np(t1))
+            np.testing.assert_array_equal(_np(nc[s]), _np(n1))
+            np.testing.assert_array_equal(_np(st[s]), _np(s1))
+
+
+def test_batch_graph_capture_replay(hg):
+    specs = synth.batch_specs(n_grids=3, rays_lo=1e3, rays_hi=5e3, leaves_lo=2e3, leaves_hi=1e4)
+    grids, os_, ks, begins = [], [], [], [0]
+    for sp in specs:
+        bp = synth.BuildParams(kind=sp["kind"], delta_max=1.0 / sp["target_leaves"], max_level=7, seed=sp["seed"])
+        grids.append(hg.load_grid(hg.build_grid(sp["model"], bp)))
+        o, k = synth.emission_rays(sp["seed"], sp["n_rays"])
+        os_.append(o)
+        ks.append(k)
+        begins.append(begins[-1] + sp["n_rays"])
+    O = _cuda(np.concatenate(os_))
+    K = _cuda(np.concatenate(ks))
+    b = hg.Batch(grids, begins)
+    ref = [_np(x) for x in b.trace(O, K)]
+    out = (torch.empty(b.n_rays, dtype=torch.float64, device="cuda"),
+           torch.empty(b.n_rays, dtype=torch.int32, device="cuda"),
+           torch.empty(b.n_rays, dtype=torch.uint8, device="cuda"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.trace(O, K, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.trace(O, K, out=out)
+    for t in out:
+        t.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    for r, x in zip(ref, out):
+        np.testing.assert_array_equal(r, _np(x))
+
+
+def test_autotune_keeps_results(hg, disk_grids):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[1]
+    O, K = _cuda(o), _cuda(k)
+    before = _np(hg.trace_rays(grid, O, K)[0])
+    cfg, ms = hg.autotune(grid, O, K)
+    assert cfg["block"] in (128, 256, 512) and cfg["schedule"] in (1, 2) and ms > 0
+    after = _np(hg.trace_rays(grid, O, K)[0])
+    np.testing.assert_array_equal(before, after)
+
+
+# ----------------------------------------------------------------------------- full-size disk grids
+
+@pytest.fixture(scope="module")
+def disk_1e6(hg):
+    out = {}
+    for kind in (0, 1):
+        model, bp, n_rays, seed = synth.workload_disk_1e6(kind)
+        H = hg.build_grid(model, bp)
+        T = oracle.build_tree(model, bp)
+        np.testing.assert_array_equal(H.child_first, T.child)
+        np.testing.assert_array_equal(H.leaf_rho, T.leaf_rho)
+        out[kind] = (hg.load_grid(H), T)
+    o, k = synth.emission_rays(seed, n_rays)
+    return model, out, o, k
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_disk_1e6_leaves_1e6_rays(hg, disk_1e6, kind):
+    model, grids, o, k = disk_1e6
+    grid, tree = grids[kind]
+    O, K = _cuda(o), _cuda(k)
+    ref = oracle.trace(tree, o, k)
+    for prec in ("fp64", "fp32k"):
+        tau, nc, st = hg.trace_rays(grid, O, K, precision=prec)
+        np.testing.assert_array_equal(_np(nc), ref["ncross"])
+        np.testing.assert_array_equal(_np(st), ref["status"])
+        _check_tau(_np(tau), ref["tau"], TAU_RTOL_FP64 if prec == "fp64" else TAU_RTOL_FP32K)
+    # full sequences on a sample of rays, traced in the same launch shape as the benchmark
+    sel = np.random.default_rng(kind).choice(o.shape[0], 20000, replace=False)
+    _compare(hg, grid, tree, o[sel], k[sel])
