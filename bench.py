@@ -1,0 +1,481 @@
+#!/usr/bin/env python
+"""Benchmark of the path-calculation hot path on GB300.
+
+One step = the whole hot path over one batch of synthetic input, for each
+grid of the workload:
+  trace_rays (locate, exit-wall walk, neighbor search, tau, crossing count),
+  <N_cross> reduction, emission (scan + fill of cell ids and segment lengths),
+  grid density at uniform points with Delta-rho, optical depth along
+  uniform-endpoint paths with Delta-tau, and the adjoint scatter.
+Grids are built and uploaded before timing; the true densities and optical
+depths of the analytic model (the reference values of Delta-rho and
+Delta-tau) are computed once before timing.
+
+Default workload: the exponential disk at ~1e6 leaves, octree and k-d tree,
+1e6 emission rays each (FP64).  ``value`` = emission rays traced through
+both grids per second of whole-step time.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload (the comparison arm).  Under torchrun every rank traces its
+own rays through replicated grids (weak scaling, no collective on the data
+path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "rays/s and Gcell-crossings/s (octree vs k-d tree), % HBM roofline, vs FP64"
+UNIT = "rays/s"
+# algorithmic bytes of the trace kernel: per crossing 6 FP64 bounds + FP64 density + the exit
+# wall's CSR range (2 x int64) + one neighbor id; per ray origin + direction in, tau + count + status out
+BYTES_PER_CROSSING = {"fp64": 48 + 8 + 16 + 4, "fp32k": 48 + 4 + 16 + 4}
+BYTES_PER_RAY = {"fp64": 48 + 8 + 4 + 1, "fp32k": 48 + 4 + 4 + 1}
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Independent rays per rank (weak scaling): rank 0 keeps the workload's own seed."""
+    return seed + 7919 * rank
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("walk.cuh", "trace.cu", "hg_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1311_0705_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the trace kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"trace_kernel_{workload}_{precision}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_b or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_b.group(1))
+
+
+def make_disk_grids(hg, threads=0):
+    grids = []
+    for kind in (synth.TREE_OCTREE, synth.TREE_KD):
+        model, bp, n_rays, seed = synth.workload_disk_1e6(kind)
+        t0 = time.time()
+        host = hg.build_grid(model, bp, threads=threads)
+        tb = time.time() - t0
+        grids.append(dict(name="octree" if kind == 0 else "kd", kind=kind, host=host, build_s=tb))
+    return model, grids, n_rays, seed
+
+
+def make_small_grids(hg, threads=0):
+    model, bp, n_rays, seed = synth.workload_disk_small()
+    grids = []
+    for kind in (synth.TREE_OCTREE, synth.TREE_KD):
+        bp.kind = kind
+        t0 = time.time()
+        host = hg.build_grid(model, bp, threads=threads)
+        grids.append(dict(name="octree" if kind == 0 else "kd", kind=kind, host=host, build_s=time.time() - t0))
+    return model, grids, n_rays, seed
+
+
+WORKLOADS = {
+    "disk-1e6": ("disk, octree (mass 1e-6, max level 12) and k-d tree (same threshold), 1e6 rays per grid",
+                 make_disk_grids),
+    "disk-1e4": ("disk, octree and k-d tree (mass 1e-4, max level 6), 1e4 rays per grid", make_small_grids),
+}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import paper_1311_0705_gb300 as hg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    desc, maker = WORKLOADS[args.workload]
+    model, grids, n_rays, seed = maker(hg)
+    n_pts = n_rays
+    n_paths = max(1, n_rays // 10)
+    prec = args.precision
+    rs = rank_seed(seed, rank)
+    o, k = synth.emission_rays(rs, n_rays)
+    pts = synth.sample_points(rs + 1, n_pts)
+    pa, pk, pl = synth.endpoint_paths(rs + 2, n_paths)
+    w = synth.adjoint_weights(rs + 3, n_rays)
+    O, K = torch.tensor(o, device=dev), torch.tensor(k, device=dev)
+    P = torch.tensor(pts, device=dev)
+    PA, PK, PL = torch.tensor(pa, device=dev), torch.tensor(pk, device=dev), torch.tensor(pl, device=dev)
+    W = torch.tensor(w, device=dev)
+    dm = hg.load_model(model)
+    # reference values of the metrics (the analytic model), computed once
+    RT = hg.model_density(dm, P)
+    TT = hg.model_tau(dm, PA, PK, PL)
+    for g in grids:
+        t0 = time.time()
+        g["grid"] = hg.load_grid(g["host"], validate=args.validate)
+        torch.cuda.synchronize()
+        g["load_s"] = time.time() - t0
+        n = n_rays
+        g["tau"] = torch.empty(n, dtype=torch.float64 if prec == "fp64" else torch.float32, device=dev)
+        g["nc"] = torch.empty(n, dtype=torch.int32, device=dev)
+        g["st"] = torch.empty(n, dtype=torch.uint8, device=dev)
+        g["ptau"] = torch.empty(n_paths, dtype=torch.float64, device=dev)
+        g["pnc"] = torch.empty(n_paths, dtype=torch.int32, device=dev)
+        g["grad"] = torch.zeros(g["grid"].n_leaves, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    kev = []  # (start, end) events around the dominant kernel
+
+    def step(record=False):
+        out = {}
+        for g in grids:
+            G = g["grid"]
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            hg.trace_rays(G, O, K, kappa=1.0, precision=prec, out=(g["tau"], g["nc"], g["st"]))
+            if record:
+                e1.record(stream)
+                kev.append((g["name"], e0, e1))
+            ncs = hg.sum_i32(g["nc"])
+            off = hg.scan_offsets(g["nc"])
+            cap = g.get("cap")
+            if cap is None:
+                cap = g["cap"] = int(off[-1].item())
+            cell, ds = hg.trace_fill(G, O, K, off, precision=prec, capacity=cap, status=g["st"])
+            _, rg = hg.sample_density(G, P)
+            drho = hg.diff_stats(RT, rg)
+            ptau, _, _ = hg.trace_rays(G, PA, PK, PL, kappa=1.0, precision="fp64", out=(g["ptau"], g["pnc"], None))
+            dtau = hg.diff_stats(TT, ptau)
+            g["grad"].zero_()
+            hg.tau_gradient(G, O, K, W, kappa=1.0, grad=g["grad"], grad_precision="fp32")
+            out[g["name"]] = (ncs, drho, dtau)
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of the timed configuration: no ray may end in an error state
+    for g in grids:
+        bits = int(hg.reduce_status(g["st"]).item())
+        if bits:
+            raise RuntimeError(f"ray status bits {bits} on {g['name']}")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = hg.launch_count()
+    barrier(dist, dev)
+    torch.cuda.synchronize()
+    step_ms = []
+    results = None
+    for s in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        results = step(record=True)
+        b.record(stream)
+        step_ms.append((a, b))
+    torch.cuda.synchronize()
+    barrier(dist, dev)
+    launches = hg.launch_count() - launches0
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in step_ms]
+    local_ms = sum(times)
+    tot_ms = max_over_ranks(dist, local_ms, dev)
+    rays_per_step = n_rays * len(grids)
+    all_rays = sum_over_ranks(dist, rays_per_step * args.steps, dev)
+    value = all_rays / (tot_ms / 1e3)
+
+    # dominant kernel: trace_rays; algorithmic bytes per launch / mean launch time
+    per = {}
+    for name, e0, e1 in kev:
+        per.setdefault(name, []).append(e0.elapsed_time(e1))
+    kern = {}
+    tot_bytes, tot_time = 0.0, 0.0
+    for g in grids:
+        cr = int(g["nc"].sum().item())
+        ms = statistics.mean(per[g["name"]])
+        byt = BYTES_PER_CROSSING[prec] * cr + BYTES_PER_RAY[prec] * n_rays
+        kern[g["name"]] = dict(leaves=g["grid"].n_leaves, build_s=round(g["build_s"], 2), load_s=round(g["load_s"], 2),
+                               mean_ncross=cr / n_rays, trace_ms=ms, trace_rays_per_s=n_rays / ms * 1e3,
+                               gcross_per_s=cr / ms / 1e6, algorithmic_bytes=byt,
+                               delta_rho=float(results[g["name"]][1][2].item()),
+                               delta_tau=float(results[g["name"]][2][2].item()))
+        tot_bytes += byt
+        tot_time += ms
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = tot_bytes / (tot_time / 1e3) / 1e9
+    traffic = recorded_traffic(args.workload, prec)
+    roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s", frac=round(achieved / peak, 4),
+                    traffic=traffic, kernel="trace_kernel (hg_trace_rays)",
+                    peak_source="measured" if "hbm_gbs" in peaks else "fallback")
+
+    # e2e: the same step through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        ho = torch.tensor(o).pin_memory()
+        hk = torch.tensor(k).pin_memory()
+        htau = [torch.empty(n_rays, dtype=g["tau"].dtype).pin_memory() for g in grids]
+        hnc = [torch.empty(n_rays, dtype=torch.int32).pin_memory() for g in grids]
+        barrier(dist, dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es = []
+        for s in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            O.copy_(ho, non_blocking=True)
+            K.copy_(hk, non_blocking=True)
+            step()
+            for j, g in enumerate(grids):
+                htau[j].copy_(g["tau"], non_blocking=True)
+                hnc[j].copy_(g["nc"], non_blocking=True)
+            b.record(stream)
+            es.append((a, b))
+        torch.cuda.synchronize()
+        barrier(dist, dev)
+        e_ms = max_over_ranks(dist, sum(x.elapsed_time(y) for x, y in es), dev)
+        h2d = 2 * n_rays * 3 * 8
+        d2h = sum(n_rays * (g["tau"].element_size() + 4) for g in grids)
+        e2e = dict(value=sum_over_ranks(dist, rays_per_step * args.steps, dev) / (e_ms / 1e3), unit=UNIT,
+                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(model, grids, o, k, pts, pa, pk, pl, w, sample=args.cpu_sample)
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=tot_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64" if prec == "fp64" else "f32+f64", data="synthetic",
+                config=dict(workload=args.workload, description=desc, rays_per_grid=n_rays, points=n_pts,
+                            paths=n_paths, precision=prec, l2="flushed between steps (512 MB write)",
+                            grids=kern),
+                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+
+def oracle_step(oracle, model, trees, o, k, pts, pa, pk, pl, w, threads):
+    """The oracle's version of one step on a sample: trace with emission (tau, counts,
+    cell sequences, adjoint accumulation), grid density at points, Delta-tau paths."""
+    for T in trees:
+        r = oracle.trace(T, o, k, emit=True, threads=threads)
+        oracle.adjoint(T.n_leaves, r["seg_off"], r["seg_cell"], r["seg_ds"], w.astype(np.float64))
+        oracle.sample_density(T, pts)
+        oracle.trace(T, pa, pk, smax=pl, threads=threads)
+
+
+def _oracle_trees(oracle, grids):
+    trees = []
+    for g in grids:
+        H = g["host"]
+        trees.append(oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho))
+    return trees
+
+
+def cpu_baseline(model, grids, o, k, pts, pa, pk, pl, w, sample: int = 200_000):
+    import oracle
+    threads = os.cpu_count() or 1
+    trees = _oracle_trees(oracle, grids)
+    n = min(sample, o.shape[0])
+    npth = max(1, n // 10)
+    rt = oracle.rho_true(model, pts[:n])  # noqa: F841  (the truth the step compares against)
+    t0 = time.perf_counter()
+    oracle_step(oracle, model, trees, o[:n], k[:n], pts[:n], pa[:npth], pk[:npth], pl[:npth], w[:n], threads)
+    dt = time.perf_counter() - t0
+    return dict(value=n * len(trees) / dt, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"{n} of the emission rays per grid (+{n} points, {npth} paths) through "
+                       f"{len(trees)} grids: trace with emission, adjoint accumulation, density, Delta-tau paths")
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import paper_1311_0705_gb300 as hg  # the grid is the workload's input; only the oracle runs below
+    desc, maker = WORKLOADS[args.workload]
+    model, grids, n_rays, seed = maker(hg)
+    threads = os.cpu_count() or 1
+    trees = _oracle_trees(oracle, grids)
+    o, k = synth.emission_rays(seed, n_rays)
+    pts = synth.sample_points(seed + 1, n_rays)
+    n_paths = max(1, n_rays // 10)
+    pa, pk, pl = synth.endpoint_paths(seed + 2, n_paths)
+    w = synth.adjoint_weights(seed + 3, n_rays)
+    n = min(args.cpu_sample, n_rays)
+    npth = max(1, n // 10)
+    for _ in range(args.warmup):
+        oracle_step(oracle, model, trees, o[:n], k[:n], pts[:n], pa[:npth], pk[:npth], pl[:npth], w[:n], threads)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        j = (s * n) % max(1, n_rays - n + 1)
+        oracle_step(oracle, model, trees, o[j:j + n], k[j:j + n], pts[j:j + n], pa[:npth], pk[:npth], pl[:npth],
+                    w[j:j + n], threads)
+    dt = time.perf_counter() - t0
+    value = n * len(trees) * args.steps / dt
+    sample = (f"per step {n} of the {n_rays} emission rays per grid (+{n} points, {npth} paths) through "
+              f"{len(trees)} grids: trace with emission, adjoint accumulation, density, Delta-tau paths")
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=dt / args.steps * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, description=desc, rays_per_grid=n_rays, precision="fp64"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=threads, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="disk-1e6")
+    ap.add_argument("--precision", choices=["fp64", "fp32k"], default="fp64")
+    ap.add_argument("--validate", action="store_true", help="validate grid descriptions at load")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -189,7 +189,7 @@ hg_status hg_grid_get_info(const hg_grid *g, hg_grid_info *out);
 typedef struct hg_trace_opts {
     int32_t precision;   /* HG_FP64 or HG_FP32K */
     int32_t block;       /* threads per block; 0 = tuned or default */
-    int32_t smem_nodes;  /* top tree nodes staged in shared memory; -1 = tuned or default */
+    int32_t smem_nodes;  /* top tree nodes staged in shared memory (clamped to 200 KB); -1 = tuned or default */
     int32_t schedule;    /* 0 = tuned or default, 1 = one ray per thread, 2 = persistent with warp refill */
     int64_t max_steps;   /* per-ray step limit; 0 = 4 * n_leaves + 64 */
 } hg_trace_opts;

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
     const float kappa32 = (float)A.kappa;
     int64_t ray = -1;
     const BatchEntry *E = nullptr;
-    int64_t max_steps = 0;
+    int32_t max_steps32 = 0;
     RayState S;
     Leaf L;
     double acc = 0.0;
@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
             }
             E = A.E + s_perm[lo];
             ray = E->ray0 + (q - s_qbeg[lo]);
-            max_steps = A.max_steps > 0 ? A.max_steps : E->max_steps;
+            {
+                const int64_t ms = A.max_steps > 0 ? A.max_steps : E->max_steps;
+                max_steps32 = (int32_t)(ms < 0x7fffffff ? ms : 0x7fffffff);
+            }
             acc = 0.0;
             acc32 = 0.0f;
             comp32 = 0.0f;
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
         {
             double ds, tex;
             int ax;
-            const int r1 = ray_exit(max_steps, S, L, &ds, &ax, &tex, &st);
+            const int r1 = ray_exit(max_steps32, S, L, &ds, &ax, &tex, &st);
             if (ds != 0.0) {
                 if (PREC == HG_FP64) {
                     acc = acc + L.rho * ds;

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A) {
     double wk = 0.0;  // kappa * w for the adjoint
     uint32_t st = 0;
     const float kappa32 = (float)A.kappa;
+    const int32_t max_steps32 = (int32_t)(A.max_steps < 0x7fffffff ? A.max_steps : 0x7fffffff);
 
     for (;;) {
         if (ray < 0) {
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A) {
             double ds;
             int ax;
             double tex;
-            const int r1 = ray_exit(A.max_steps, S, L, &ds, &ax, &tex, &st);
+            const int r1 = ray_exit(max_steps32, S, L, &ds, &ax, &tex, &st);
             if (ds != 0.0) {
                 if (MODE == MODE_TAU) {
                     if (PREC == HG_FP64) {
@@ -208,12 +209,9 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
         set_error("schedule must be 1 or 2");
         return HG_EINVAL;
     }
-    smem_nodes = (int)std::min<int64_t>(smem_nodes, g->d.n_nodes);
+    // clamp to the node count and to 200 KB of shared memory
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
-    if ((int64_t)smem_nodes * node_bytes > 200 * 1024) {
-        set_error("smem_nodes exceeds 200 KB of shared memory");
-        return HG_EINVAL;
-    }
+    smem_nodes = (int)std::min<int64_t>(std::min<int64_t>(smem_nodes, g->d.n_nodes), (200 * 1024) / node_bytes);
     return HG_OK;
 }
 

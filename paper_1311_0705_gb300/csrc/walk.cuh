@@ -133,7 +133,7 @@ struct RayState {
     double o0, o1, o2, k0, k1, k2, ik0, ik1, ik2;
     double tend, tcur;
     int32_t cur;
-    int64_t steps;
+    int32_t steps;
 };
 
 enum { WALK_GO = 0, WALK_END = 1 };
@@ -211,7 +211,7 @@ __device__ __forceinline__ int ray_init(const DevGrid &G, const unsigned char *s
 // important, Sect. 2.3).  Sets *ds (0: nothing to record) and *ax (-1 when
 // the path ends inside the leaf).  Returns WALK_END when the walk stops
 // after this leaf's segment, WALK_GO when ray_advance should follow.
-__device__ __forceinline__ int ray_exit(int64_t max_steps, RayState &S, const Leaf &L, double *ds, int *ax_out,
+__device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Leaf &L, double *ds, int *ax_out,
                                         double *tex_out, uint32_t *st) {
     *ds = 0.0;
     *ax_out = -1;
@@ -277,29 +277,27 @@ __device__ __forceinline__ int ray_advance(const DevGrid &G, const unsigned char
     // an exit point on the domain surface with the direction pointing out ends the path
     if (!in_axis(p1, G.dlo[b1], G.dhi[b1], kb1, true) || !in_axis(p2, G.dlo[b2], G.dhi[b2], kb2, true))
         return WALK_END;
-    // neighbor-list search: the list head is stored in the leaf itself
-    Leaf N;
-    load_leaf(G.rec, nxt, N);
+    // neighbor-list search.  What is still needed from the current leaf is
+    // taken out first; each candidate is then loaded straight into L.
+    const int cw = L.cnt(w);
+    uint32_t off = L.base;
+    for (int v = 0; v < w; v++) {
+        const int c = L.cnt(v);
+        if (c >= 2 && c <= G.scan_limit) off += (uint32_t)(c - 1);
+    }
     const uint32_t ub1 = 1u << b1, ub2 = 1u << b2;
-    if (in_axis(p1, N.lo(b1), N.hi(b1), kb1, N.flags() & ub1) && in_axis(p2, N.lo(b2), N.hi(b2), kb2, N.flags() & ub2)) {
+    load_leaf(G.rec, nxt, L);  // the list head is stored in the leaf itself
+    if (in_axis(p1, L.lo(b1), L.hi(b1), kb1, L.flags() & ub1) && in_axis(p2, L.lo(b2), L.hi(b2), kb2, L.flags() & ub2)) {
         S.cur = nxt;
-        L = N;
         return WALK_GO;
     }
-    const int cw = L.cnt(w);
     if (cw >= 2 && cw <= G.scan_limit) {
-        uint32_t off = L.base;
-        for (int v = 0; v < w; v++) {
-            const int c = L.cnt(v);
-            if (c >= 2 && c <= G.scan_limit) off += (uint32_t)(c - 1);
-        }
         for (int e = 0; e < cw - 1; e++) {
             const int32_t j = __ldg(G.tail + off + e);
-            load_leaf(G.rec, j, N);
-            if (in_axis(p1, N.lo(b1), N.hi(b1), kb1, N.flags() & ub1) &&
-                in_axis(p2, N.lo(b2), N.hi(b2), kb2, N.flags() & ub2)) {
+            load_leaf(G.rec, j, L);
+            if (in_axis(p1, L.lo(b1), L.hi(b1), kb1, L.flags() & ub1) &&
+                in_axis(p2, L.lo(b2), L.hi(b2), kb2, L.flags() & ub2)) {
                 S.cur = j;
-                L = N;
                 return WALK_GO;
             }
         }
