@@ -201,12 +201,12 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
                 const int32_t c = D.child_first[i];
                 K[i].child = c;
                 if (c < 0) {
-                    K[i].split = 0.0;
+                    K[i].split = 0;
                     K[i].info = D.node_leaf[i];
                 } else {
                     int ax = 0;
                     while (ax < 2 && D.node_hi[3 * (int64_t)c + ax] == D.node_hi[3 * i + ax]) ax++;
-                    K[i].split = D.node_hi[3 * (int64_t)c + ax];
+                    K[i].split = hg::host_okey(D.node_hi[3 * (int64_t)c + ax]);
                     K[i].info = ax;
                 }
             }
@@ -217,7 +217,7 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
                 const int32_t c = D.child_first[i];
                 O[i].child = c;
                 O[i].leaf = D.node_leaf[i];
-                for (int a = 0; a < 3; a++) O[i].s[a] = (c < 0) ? 0.0 : D.node_hi[3 * (int64_t)c + a];
+                for (int a = 0; a < 3; a++) O[i].s[a] = (c < 0) ? 0 : hg::host_okey(D.node_hi[3 * (int64_t)c + a]);
             }
         }
         // leaf records and neighbor-list tails
@@ -233,9 +233,9 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
             std::memset(&R, 0, sizeof(R));
             const int64_t nd = leaf_node[i];
             for (int a = 0; a < 3; a++) {
-                R.lo[a] = D.node_lo[3 * nd + a];
-                R.hi[a] = D.node_hi[3 * nd + a];
-                if (R.hi[a] == dhi[a]) R.flags |= (uint8_t)(1u << a);
+                R.lo[a] = hg::host_okey(D.node_lo[3 * nd + a]);
+                R.hi[a] = hg::host_okey(D.node_hi[3 * nd + a]);
+                if (D.node_hi[3 * nd + a] == dhi[a]) R.flags |= (uint8_t)(1u << a);
             }
             R.rho = D.leaf_rho[i];
             R.rho32 = (float)D.leaf_rho[i];
@@ -281,6 +281,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
         for (int a = 0; a < 3; a++) {
             G.dlo[a] = D.node_lo[a];
             G.dhi[a] = D.node_hi[a];
+            G.klo[a] = hg::host_okey(G.dlo[a]);
+            G.khi[a] = hg::host_okey(G.dhi[a]);
         }
         G.n_leaves = nl;
         G.n_nodes = n;

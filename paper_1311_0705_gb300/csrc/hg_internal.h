@@ -12,6 +12,15 @@
 namespace hg {
 
 void set_error(const char *fmt, ...);
+
+// Order-preserving integer key of a non-NaN double (host side of the map
+// the kernels use): a < b <=> key(a) < key(b), and -0.0 maps like +0.0.
+inline long long host_okey(double x) {
+    long long b;
+    std::memcpy(&b, &x, 8);
+    const long long k = b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+    return k == -1LL ? 0LL : k;
+}
 void note_launches(int64_t n);
 
 // Leaf record in HBM: 96 bytes = three 32-byte sectors, so a step that
@@ -19,14 +28,17 @@ void note_launches(int64_t n);
 //   sector 0: lo.x lo.y lo.z hi.x
 //   sector 1: hi.y hi.z rho rho32 nbr_base
 //   sector 2: first[6] cnt[6] flags pad
+// Bounds are stored as order-preserving integer keys of their FP64 values
+// (the sign bit kept, the other bits flipped for negative values, -0 stored
+// as +0), so that the kernels compare them with integer instructions.
 // first[w] is the head of wall w's neighbor list (the largest overlap,
 // Sect. 2.3), -1 when the wall lies on the domain boundary.  cnt[w] is the
 // list length, saturated at 255; lists of length 2..scan_limit keep
 // entries 1.. in the tail array starting at nbr_base, walls in order.
 // flags bit a: hi on axis a equals the domain's upper bound.
 struct alignas(32) LeafRec {
-    double lo[3];
-    double hi[3];
+    int64_t lo[3];
+    int64_t hi[3];
     double rho;
     float rho32;
     uint32_t nbr_base;
@@ -37,16 +49,17 @@ struct alignas(32) LeafRec {
 };
 static_assert(sizeof(LeafRec) == 96, "leaf record must be three sectors");
 
-// Descent nodes: k-d 16 B, octree 32 B.  child = first child index in the
-// node list (children contiguous) or -1 for a leaf; info/leaf = leaf id for
-// a leaf, split axis for an internal k-d node.
+// Descent nodes: k-d 16 B, octree 32 B.  Split planes are stored as keys
+// like the leaf bounds.  child = first child index in the node list
+// (children contiguous) or -1 for a leaf; info/leaf = leaf id for a leaf,
+// split axis for an internal k-d node.
 struct alignas(16) KdNode {
-    double split;
+    int64_t split;
     int32_t child;
     int32_t info;
 };
 struct alignas(16) OctNode {
-    double s[3];
+    int64_t s[3];
     int32_t child;
     int32_t leaf;
 };
@@ -58,6 +71,7 @@ struct DevGrid {
     const int32_t *tail;
     const void *nodes;
     double dlo[3], dhi[3];
+    long long klo[3], khi[3];  // keys of the domain bounds
     int64_t n_leaves;
     int64_t n_nodes;
     int32_t kind;

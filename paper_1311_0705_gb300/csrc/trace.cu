@@ -280,9 +280,12 @@ __global__ void sample_kernel(const DevGrid G, int64_t n, const double *__restri
     extern __shared__ __align__(16) unsigned char smem[];
     stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double p0 = pts[3 * i], p1 = pts[3 * i + 1], p2 = pts[3 * i + 2];
+        const long long p0 = okey(pts[3 * i]), p1 = okey(pts[3 * i + 1]), p2 = okey(pts[3 * i + 2]);
         int32_t c = -1;
-        if (in_domain(G, p0, p1, p2, 0.0, 0.0, 0.0)) c = descend<KIND>(G, smem, n_smem, p0, p1, p2, 0.0, 0.0, 0.0);
+        // a point query uses the half-open rule of a zero direction
+        if (in_axis(p0, G.klo[0], G.khi[0], false, false, true) && in_axis(p1, G.klo[1], G.khi[1], false, false, true) &&
+            in_axis(p2, G.klo[2], G.khi[2], false, false, true))
+            c = descend<KIND>(G, smem, n_smem, p0, p1, p2, 0u);
         if (cell) cell[i] = c;
         rho[i] = (c >= 0) ? __ldg(&G.rec[c].rho) : 0.0;
     }

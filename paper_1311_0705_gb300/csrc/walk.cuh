@@ -2,6 +2,15 @@
 // (Sect. 2.3): top-down location of the first leaf, then one exit-wall test
 // per crossed leaf and the next leaf from that wall's neighbor list.
 //
+// GB300 runs FP64 add, multiply and compare at about 1/64 of its FP32 rate
+// (and 1/16 of its 64-bit integer compare rate), so every comparison of two
+// FP64 values is made on order-preserving 64-bit integer keys of those
+// values (see okey), which gives exactly the IEEE result (-0 and +0 share a
+// key), and only the arithmetic of the contract stays in FP64: the time to
+// a wall ahead, the exit point, the segment length and the running sum.
+// Leaf bounds and descent split planes are stored as keys; a wall needed in
+// arithmetic is turned back into its double by the inverse map.
+//
 // Every translation unit including this file is compiled with -fmad=false,
 // so each FP64 multiply and add below is rounded separately, as the
 // arithmetic contract in hgrt.h states.
@@ -14,7 +23,21 @@
 
 namespace hg {
 
-__device__ __forceinline__ double sel3(int a, double v0, double v1, double v2) {
+// Order-preserving key of a non-NaN double: a < b  <=>  okey(a) < okey(b),
+// a == b <=> okey(a) == okey(b) (so -0.0 and +0.0 both map to 0).
+__device__ __forceinline__ long long okey(double x) {
+    const long long b = __double_as_longlong(x);
+    const long long k = b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+    return k == -1LL ? 0LL : k;
+}
+// Inverse of okey (the double with that key; +0.0 for key 0).
+__device__ __forceinline__ double kdouble(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+constexpr long long KEY_INF = 0x7ff0000000000000LL;  // okey(+inf)
+
+template <class T>
+__device__ __forceinline__ T sel3(int a, T v0, T v1, T v2) {
     return a == 0 ? v0 : (a == 1 ? v1 : v2);
 }
 __device__ __forceinline__ int32_t sel6(int w, int32_t v0, int32_t v1, int32_t v2, int32_t v3, int32_t v4,
@@ -28,9 +51,9 @@ __device__ __forceinline__ int32_t sel6(int w, int32_t v0, int32_t v1, int32_t v
     return r;
 }
 
-// One leaf record held in registers.
+// One leaf record held in registers (bounds as keys).
 struct Leaf {
-    double lo0, lo1, lo2, hi0, hi1, hi2;
+    long long lo0, lo1, lo2, hi0, hi1, hi2;
     double rho;
     float rho32;
     uint32_t base;
@@ -42,14 +65,15 @@ struct Leaf {
         return w < 4 ? (int)((c03 >> (8 * w)) & 255u) : (int)((c45 >> (8 * (w - 4))) & 255u);
     }
     __device__ __forceinline__ uint32_t flags() const { return (c45 >> 16) & 255u; }
-    __device__ __forceinline__ double lo(int a) const { return sel3(a, lo0, lo1, lo2); }
-    __device__ __forceinline__ double hi(int a) const { return sel3(a, hi0, hi1, hi2); }
+    __device__ __forceinline__ long long lo(int a) const { return sel3(a, lo0, lo1, lo2); }
+    __device__ __forceinline__ long long hi(int a) const { return sel3(a, hi0, hi1, hi2); }
 };
 
 // Fetch a whole 96-byte record with six 16-byte read-only loads.
 __device__ __forceinline__ void load_leaf(const LeafRec *__restrict__ R, int32_t id, Leaf &L) {
-    const double2 *q = reinterpret_cast<const double2 *>(R + id);
-    const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    const longlong2 *q = reinterpret_cast<const longlong2 *>(R + id);
+    const longlong2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    const double2 d = __ldg(reinterpret_cast<const double2 *>(q + 3));
     const int4 *qi = reinterpret_cast<const int4 *>(R + id) + 4;
     const int4 e = __ldg(qi), f = __ldg(qi + 1);
     L.lo0 = a.x;
@@ -72,56 +96,53 @@ __device__ __forceinline__ void load_leaf(const LeafRec *__restrict__ R, int32_t
     L.c45 = (uint32_t)f.w;
 }
 
-// Direction-aware containment on one axis: l < p < h, or p == l with k >= 0,
-// or p == h with k < 0, or p == h on the domain's upper face with k == 0.
-__device__ __forceinline__ bool in_axis(double p, double l, double h, double k, bool upper_face) {
-    return (l < p && p < h) || (p == l && k >= 0.0) || (p == h && (k < 0.0 || (k == 0.0 && upper_face)));
+// Direction signs of a ray: bit a = d_a > 0, bit 3+a = d_a < 0 (neither:
+// d_a is a signed zero).
+__device__ __forceinline__ bool dpos(uint32_t s, int a) { return (s >> a) & 1u; }
+__device__ __forceinline__ bool dneg(uint32_t s, int a) { return (s >> (3 + a)) & 1u; }
+
+// Direction-aware containment on one axis (keys): l < p < h, or p == l with
+// d >= 0, or p == h with d < 0, or p == h on the domain's upper face with d == 0.
+__device__ __forceinline__ bool in_axis(long long p, long long l, long long h, bool pos, bool neg, bool upper_face) {
+    return (l < p && p < h) || (p == l && !neg) || (p == h && (neg || (!pos && upper_face)));
 }
 
-__device__ __forceinline__ bool in_domain(const DevGrid &G, double p0, double p1, double p2, double k0, double k1,
-                                          double k2) {
-    return in_axis(p0, G.dlo[0], G.dhi[0], k0, true) && in_axis(p1, G.dlo[1], G.dhi[1], k1, true) &&
-           in_axis(p2, G.dlo[2], G.dhi[2], k2, true);
-}
-
-// Top-down descent (Sect. 2.3).  The first n_smem nodes of the list (the top
-// levels, since the list is breadth first) are read from shared memory.
+// Top-down descent (Sect. 2.3) on keys.  The first n_smem nodes of the list
+// (the top levels, since the list is breadth first) come from shared memory.
 // KIND: HG_OCTREE, HG_KDTREE, or 2 = decided at run time from G.kind.
 template <int KIND>
-__device__ __forceinline__ int32_t descend(const DevGrid &G, const unsigned char *snodes, int n_smem, double p0,
-                                           double p1, double p2, double k0, double k1, double k2) {
+__device__ __forceinline__ int32_t descend(const DevGrid &G, const unsigned char *snodes, int n_smem, long long p0,
+                                           long long p1, long long p2, uint32_t sg) {
     const bool kd = (KIND == 2) ? (G.kind == HG_KDTREE) : (KIND == HG_KDTREE);
     int32_t nd = 0;
     for (int it = 0; it <= G.max_depth; it++) {
         if (kd) {
-            double2 v;
+            longlong2 v;
             if (nd < n_smem)
-                v = reinterpret_cast<const double2 *>(snodes)[nd];
+                v = reinterpret_cast<const longlong2 *>(snodes)[nd];
             else
-                v = __ldg(reinterpret_cast<const double2 *>(G.nodes) + nd);
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(v.y);
-            const int32_t child = (int32_t)(uint32_t)(bits & 0xffffffffULL);
-            const int32_t info = (int32_t)(uint32_t)(bits >> 32);
+                v = __ldg(reinterpret_cast<const longlong2 *>(G.nodes) + nd);
+            const int32_t child = (int32_t)(uint32_t)((unsigned long long)v.y & 0xffffffffULL);
+            const int32_t info = (int32_t)(uint32_t)((unsigned long long)v.y >> 32);
             if (child < 0) return info;
-            const double pa = sel3(info, p0, p1, p2), ka = sel3(info, k0, k1, k2);
-            const bool up = (pa > v.x) || (pa == v.x && ka >= 0.0);
+            const long long pa = sel3(info, p0, p1, p2);
+            const bool up = (pa > v.x) || (pa == v.x && !dneg(sg, info));
             nd = child + (up ? 1 : 0);
         } else {
-            double2 v0, v1;
+            longlong2 v0, v1;
             if (nd < n_smem) {
-                v0 = reinterpret_cast<const double2 *>(snodes)[2 * nd];
-                v1 = reinterpret_cast<const double2 *>(snodes)[2 * nd + 1];
+                v0 = reinterpret_cast<const longlong2 *>(snodes)[2 * nd];
+                v1 = reinterpret_cast<const longlong2 *>(snodes)[2 * nd + 1];
             } else {
-                v0 = __ldg(reinterpret_cast<const double2 *>(G.nodes) + 2 * nd);
-                v1 = __ldg(reinterpret_cast<const double2 *>(G.nodes) + 2 * nd + 1);
+                v0 = __ldg(reinterpret_cast<const longlong2 *>(G.nodes) + 2 * nd);
+                v1 = __ldg(reinterpret_cast<const longlong2 *>(G.nodes) + 2 * nd + 1);
             }
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(v1.y);
-            const int32_t child = (int32_t)(uint32_t)(bits & 0xffffffffULL);
-            const int32_t leaf = (int32_t)(uint32_t)(bits >> 32);
+            const int32_t child = (int32_t)(uint32_t)((unsigned long long)v1.y & 0xffffffffULL);
+            const int32_t leaf = (int32_t)(uint32_t)((unsigned long long)v1.y >> 32);
             if (child < 0) return leaf;
-            const int ci = ((p0 > v0.x) || (p0 == v0.x && k0 >= 0.0) ? 1 : 0) |
-                           ((p1 > v0.y) || (p1 == v0.y && k1 >= 0.0) ? 2 : 0) |
-                           ((p2 > v1.x) || (p2 == v1.x && k2 >= 0.0) ? 4 : 0);
+            const int ci = ((p0 > v0.x) || (p0 == v0.x && !dneg(sg, 0)) ? 1 : 0) |
+                           ((p1 > v0.y) || (p1 == v0.y && !dneg(sg, 1)) ? 2 : 0) |
+                           ((p2 > v1.x) || (p2 == v1.x && !dneg(sg, 2)) ? 4 : 0);
             nd = child + ci;
         }
     }
@@ -131,7 +152,9 @@ __device__ __forceinline__ int32_t descend(const DevGrid &G, const unsigned char
 // Per-ray walking state.
 struct RayState {
     double o0, o1, o2, k0, k1, k2, ik0, ik1, ik2;
-    double tend, tcur;
+    long long ktend;  // key of the path end (KEY_INF: walk to the domain exit)
+    long long ktcur;  // key of the current time
+    uint32_t sg;      // direction sign bits
     int32_t cur;
     int32_t steps;
 };
@@ -139,32 +162,37 @@ struct RayState {
 enum { WALK_GO = 0, WALK_END = 1 };
 
 // Set up a ray: checks, clip against the domain, first leaf.  Returns
-// WALK_GO with S.cur and L filled, or WALK_END (status in *st).
+// WALK_GO with S.cur and L filled, or WALK_END (status in *st).  Runs once
+// per ray, so it keeps plain FP64 compares.
 template <int KIND>
 __device__ __forceinline__ int ray_init(const DevGrid &G, const unsigned char *snodes, int n_smem,
                                         const double *__restrict__ o, const double *__restrict__ d,
                                         const double *__restrict__ smax, int64_t r, RayState &S, Leaf &L,
                                         uint32_t *st) {
     *st = 0;
-    S.o0 = o[3 * r];
-    S.o1 = o[3 * r + 1];
-    S.o2 = o[3 * r + 2];
-    S.k0 = d[3 * r];
-    S.k1 = d[3 * r + 1];
-    S.k2 = d[3 * r + 2];
-    S.tend = smax ? smax[r] : CUDART_INF;
-    if (!(isfinite(S.o0) && isfinite(S.o1) && isfinite(S.o2) && isfinite(S.k0) && isfinite(S.k1) &&
-          isfinite(S.k2)) ||
-        (S.k0 == 0.0 && S.k1 == 0.0 && S.k2 == 0.0) || isnan(S.tend)) {
+    double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
+    const double kk[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+    const double tend = smax ? smax[r] : CUDART_INF;
+    if (!(isfinite(oo[0]) && isfinite(oo[1]) && isfinite(oo[2]) && isfinite(kk[0]) && isfinite(kk[1]) &&
+          isfinite(kk[2])) ||
+        (kk[0] == 0.0 && kk[1] == 0.0 && kk[2] == 0.0) || isnan(tend)) {
         *st = HG_RAY_BADINPUT;
         return WALK_END;
     }
-    S.ik0 = (S.k0 != 0.0) ? 1.0 / S.k0 : 0.0;
-    S.ik1 = (S.k1 != 0.0) ? 1.0 / S.k1 : 0.0;
-    S.ik2 = (S.k2 != 0.0) ? 1.0 / S.k2 : 0.0;
+    // a signed-zero origin coordinate gives the same comparisons and sums as +0
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        if (oo[a] == 0.0) oo[a] = 0.0;
+    double ik[3];
+    uint32_t sg = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        ik[a] = (kk[a] != 0.0) ? 1.0 / kk[a] : 0.0;
+        sg |= (kk[a] > 0.0 ? 1u : 0u) << a;
+        sg |= (kk[a] < 0.0 ? 1u : 0u) << (3 + a);
+    }
     double ts = 0.0, tout = CUDART_INF;
     int entry = -1;
-    const double oo[3] = {S.o0, S.o1, S.o2}, kk[3] = {S.k0, S.k1, S.k2}, ik[3] = {S.ik0, S.ik1, S.ik2};
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         if (kk[a] == 0.0) {
@@ -179,32 +207,53 @@ __device__ __forceinline__ int ray_init(const DevGrid &G, const unsigned char *s
         }
         if (tf < tout) tout = tf;
     }
-    if (!(ts < tout) || !(ts < S.tend)) return WALK_END;
-    double p[3];
+    if (!(ts < tout) || !(ts < tend)) return WALK_END;
+    long long p[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
+        double v;
         if (entry < 0) {
-            p[a] = oo[a];
+            v = oo[a];
         } else if (a == entry) {
-            p[a] = (kk[a] > 0.0) ? G.dlo[a] : G.dhi[a];
+            v = (kk[a] > 0.0) ? G.dlo[a] : G.dhi[a];
         } else {
-            double v = oo[a] + kk[a] * ts;
+            v = oo[a] + kk[a] * ts;
             if (v < G.dlo[a]) v = G.dlo[a];
             if (v > G.dhi[a]) v = G.dhi[a];
-            p[a] = v;
         }
+        p[a] = okey(v);
     }
-    if (!in_domain(G, p[0], p[1], p[2], S.k0, S.k1, S.k2)) return WALK_END;
-    const int32_t c = descend<KIND>(G, snodes, n_smem, p[0], p[1], p[2], S.k0, S.k1, S.k2);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        if (!in_axis(p[a], okey(G.dlo[a]), okey(G.dhi[a]), dpos(sg, a), dneg(sg, a), true)) return WALK_END;
+    const int32_t c = descend<KIND>(G, snodes, n_smem, p[0], p[1], p[2], sg);
     if (c < 0) {
         *st = HG_RAY_LOST;
         return WALK_END;
     }
+    S.o0 = oo[0];
+    S.o1 = oo[1];
+    S.o2 = oo[2];
+    S.k0 = kk[0];
+    S.k1 = kk[1];
+    S.k2 = kk[2];
+    S.ik0 = ik[0];
+    S.ik1 = ik[1];
+    S.ik2 = ik[2];
+    S.sg = sg;
+    S.ktend = okey(tend);
+    S.ktcur = okey(ts);
     S.cur = c;
-    S.tcur = ts;
     S.steps = 0;
     load_leaf(G.rec, c, L);
     return WALK_GO;
+}
+
+// Key of the time to the wall ahead on one axis (KEY_INF when d_a == 0:
+// that axis never exits).
+__device__ __forceinline__ long long wall_time(bool pos, bool neg, long long lo, long long hi, double o, double ik) {
+    if (!(pos || neg)) return KEY_INF;
+    return okey((kdouble(pos ? hi : lo) - o) * ik);
 }
 
 // Exit-wall test of the current leaf (the step the paper calls the most
@@ -220,32 +269,25 @@ __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Le
         return WALK_END;
     }
     S.steps++;
-    double tex = CUDART_INF;
+    const uint32_t sg = S.sg;
+    const long long ct0 = wall_time(dpos(sg, 0), dneg(sg, 0), L.lo0, L.hi0, S.o0, S.ik0);
+    const long long ct1 = wall_time(dpos(sg, 1), dneg(sg, 1), L.lo1, L.hi1, S.o1, S.ik1);
+    const long long ct2 = wall_time(dpos(sg, 2), dneg(sg, 2), L.lo2, L.hi2, S.o2, S.ik2);
+    // smallest time, ties to the lower axis; the path end only when strictly smaller
+    long long kt = KEY_INF;
     int ax = -1;
-    if (S.k0 != 0.0) {
-        const double t = ((S.k0 > 0.0 ? L.hi0 : L.lo0) - S.o0) * S.ik0;
-        if (t < tex) { tex = t; ax = 0; }
-    }
-    if (S.k1 != 0.0) {
-        const double t = ((S.k1 > 0.0 ? L.hi1 : L.lo1) - S.o1) * S.ik1;
-        if (t < tex) { tex = t; ax = 1; }
-    }
-    if (S.k2 != 0.0) {
-        const double t = ((S.k2 > 0.0 ? L.hi2 : L.lo2) - S.o2) * S.ik2;
-        if (t < tex) { tex = t; ax = 2; }
-    }
-    if (S.tend < tex) {
-        tex = S.tend;
-        ax = -1;
-    }
-    if (tex < S.tcur) tex = S.tcur;
-    *ds = tex - S.tcur;
-    S.tcur = tex;
+    if (ct0 < kt) { kt = ct0; ax = 0; }
+    if (ct1 < kt) { kt = ct1; ax = 1; }
+    if (ct2 < kt) { kt = ct2; ax = 2; }
+    if (S.ktend < kt) { kt = S.ktend; ax = -1; }
+    if (kt < S.ktcur) kt = S.ktcur;
+    const double tex = kdouble(kt);
+    *ds = tex - kdouble(S.ktcur);
+    S.ktcur = kt;
     *ax_out = ax;
     *tex_out = tex;
     if (ax < 0) return WALK_END;
-    const double kax = sel3(ax, S.k0, S.k1, S.k2);
-    if (L.first(2 * ax + (kax > 0.0 ? 1 : 0)) < 0) return WALK_END;  // exit wall on the domain boundary
+    if (L.first(2 * ax + (dpos(sg, ax) ? 1 : 0)) < 0) return WALK_END;  // exit wall on the domain boundary
     return WALK_GO;
 }
 
@@ -256,26 +298,29 @@ __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Le
 template <int KIND>
 __device__ __forceinline__ int ray_advance(const DevGrid &G, const unsigned char *snodes, int n_smem, RayState &S,
                                            Leaf &L, int ax, double tex, uint32_t *st) {
-    const double kax = sel3(ax, S.k0, S.k1, S.k2);
-    const int w = 2 * ax + (kax > 0.0 ? 1 : 0);
+    const uint32_t sg = S.sg;
+    const bool pax = dpos(sg, ax);
+    const int w = 2 * ax + (pax ? 1 : 0);
     const int32_t nxt = L.first(w);
-    // exit point: the wall on the exit axis, clamped o + k t on the others
+    // exit point: the wall on the exit axis, o + d t clamped to the leaf on the others
     const int b1 = (ax == 0) ? 1 : 0;
     const int b2 = (ax == 2) ? 1 : 2;
-    const double wall = kax > 0.0 ? L.hi(ax) : L.lo(ax);
-    const double ob1 = sel3(b1, S.o0, S.o1, S.o2), kb1 = sel3(b1, S.k0, S.k1, S.k2);
-    const double ob2 = sel3(b2, S.o0, S.o1, S.o2), kb2 = sel3(b2, S.k0, S.k1, S.k2);
-    double p1 = ob1 + kb1 * tex;
-    double p2 = ob2 + kb2 * tex;
+    const long long wall = pax ? L.hi(ax) : L.lo(ax);
+    long long p1, p2;
     {
-        const double l1 = L.lo(b1), h1 = L.hi(b1), l2 = L.lo(b2), h2 = L.hi(b2);
+        const double ob1 = sel3(b1, S.o0, S.o1, S.o2), kb1 = sel3(b1, S.k0, S.k1, S.k2);
+        const double ob2 = sel3(b2, S.o0, S.o1, S.o2), kb2 = sel3(b2, S.k0, S.k1, S.k2);
+        p1 = okey(ob1 + kb1 * tex);
+        p2 = okey(ob2 + kb2 * tex);
+        const long long l1 = L.lo(b1), h1 = L.hi(b1), l2 = L.lo(b2), h2 = L.hi(b2);
         if (p1 < l1) p1 = l1;
         if (p1 > h1) p1 = h1;
         if (p2 < l2) p2 = l2;
         if (p2 > h2) p2 = h2;
     }
+    const bool pos1 = dpos(sg, b1), neg1 = dneg(sg, b1), pos2 = dpos(sg, b2), neg2 = dneg(sg, b2);
     // an exit point on the domain surface with the direction pointing out ends the path
-    if (!in_axis(p1, G.dlo[b1], G.dhi[b1], kb1, true) || !in_axis(p2, G.dlo[b2], G.dhi[b2], kb2, true))
+    if (!in_axis(p1, G.klo[b1], G.khi[b1], pos1, neg1, true) || !in_axis(p2, G.klo[b2], G.khi[b2], pos2, neg2, true))
         return WALK_END;
     // neighbor-list search.  What is still needed from the current leaf is
     // taken out first; each candidate is then loaded straight into L.
@@ -287,7 +332,8 @@ __device__ __forceinline__ int ray_advance(const DevGrid &G, const unsigned char
     }
     const uint32_t ub1 = 1u << b1, ub2 = 1u << b2;
     load_leaf(G.rec, nxt, L);  // the list head is stored in the leaf itself
-    if (in_axis(p1, L.lo(b1), L.hi(b1), kb1, L.flags() & ub1) && in_axis(p2, L.lo(b2), L.hi(b2), kb2, L.flags() & ub2)) {
+    if (in_axis(p1, L.lo(b1), L.hi(b1), pos1, neg1, L.flags() & ub1) &&
+        in_axis(p2, L.lo(b2), L.hi(b2), pos2, neg2, L.flags() & ub2)) {
         S.cur = nxt;
         return WALK_GO;
     }
@@ -295,18 +341,18 @@ __device__ __forceinline__ int ray_advance(const DevGrid &G, const unsigned char
         for (int e = 0; e < cw - 1; e++) {
             const int32_t j = __ldg(G.tail + off + e);
             load_leaf(G.rec, j, L);
-            if (in_axis(p1, L.lo(b1), L.hi(b1), kb1, L.flags() & ub1) &&
-                in_axis(p2, L.lo(b2), L.hi(b2), kb2, L.flags() & ub2)) {
+            if (in_axis(p1, L.lo(b1), L.hi(b1), pos1, neg1, L.flags() & ub1) &&
+                in_axis(p2, L.lo(b2), L.hi(b2), pos2, neg2, L.flags() & ub2)) {
                 S.cur = j;
                 return WALK_GO;
             }
         }
     }
     // edge or corner exit, or a long list: locate the exit point top-down
-    const double q0 = (ax == 0) ? wall : (b1 == 0 ? p1 : p2);
-    const double q1 = (ax == 1) ? wall : (b1 == 1 ? p1 : p2);
-    const double q2 = (ax == 2) ? wall : p2;
-    const int32_t j = descend<KIND>(G, snodes, n_smem, q0, q1, q2, S.k0, S.k1, S.k2);
+    const long long q0 = (ax == 0) ? wall : (b1 == 0 ? p1 : p2);
+    const long long q1 = (ax == 1) ? wall : (b1 == 1 ? p1 : p2);
+    const long long q2 = (ax == 2) ? wall : p2;
+    const int32_t j = descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg);
     if (j < 0) {
         *st = HG_RAY_LOST;
         return WALK_END;
