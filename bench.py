@@ -194,10 +194,24 @@ def make_small_grids(hg, threads=0):
     return model, grids, n_rays, seed
 
 
+def make_torus_grid(hg, threads=0):
+    model, bp, n_rays, seed = synth.workload_torus_1e7(max_level=TORUS_MAX_LEVEL)
+    t0 = time.time()
+    host = hg.build_grid(model, bp, threads=threads)
+    return model, [dict(name="kd", kind=1, host=host, build_s=time.time() - t0)], n_rays, seed
+
+
+# max level of the torus workload: 9 gives 8.4e6 leaves (10 would give ~3e7)
+TORUS_MAX_LEVEL = 9
+
 WORKLOADS = {
     "disk-1e6": ("disk, octree (mass 1e-6, max level 12) and k-d tree (same threshold), 1e6 rays per grid",
                  make_disk_grids),
     "disk-1e4": ("disk, octree and k-d tree (mass 1e-4, max level 6), 1e4 rays per grid", make_small_grids),
+    "torus-1e7": ("ring torus + 1000 clumps, k-d tree (mass 1e-7, tau 0.5, q 0.9, max level 9, ~8.4e6 leaves), "
+                  "1e7 rays: FP32-Kahan and FP64 passes plus the adjoint", make_torus_grid),
+    "batch-64": ("64 grids (octree/k-d, disk/ring/clumps, seeded), 1e5-1e7 rays each, one persistent launch",
+                 None),
 }
 
 
@@ -384,6 +398,249 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- torus and batch workloads
+
+def _timed_steps(torch, stream, steps, flush, fn):
+    """Run ``steps`` calls of fn with an L2 flush before each; returns per-step ms (CUDA events)."""
+    ev = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _peak():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_torus(args):
+    import torch
+    import paper_1311_0705_gb300 as hg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    desc, maker = WORKLOADS[args.workload]
+    model, grids, n_rays, seed = maker(hg)
+    g = grids[0]
+    t0 = time.time()
+    G = hg.load_grid(g["host"], validate=args.validate)
+    torch.cuda.synchronize()
+    load_s = time.time() - t0
+    rs = rank_seed(seed, rank)
+    o, k = synth.emission_rays(rs, n_rays)
+    w = synth.adjoint_weights(rs + 3, n_rays)
+    O, K, W = torch.tensor(o, device=dev), torch.tensor(k, device=dev), torch.tensor(w, device=dev)
+    t32 = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    t64 = torch.empty(n_rays, dtype=torch.float64, device=dev)
+    nc = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    nc64 = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    st = torch.empty(n_rays, dtype=torch.uint8, device=dev)
+    grad = torch.zeros(G.n_leaves, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    kev = {"fp32k": [], "fp64": []}
+
+    def step(record=False):
+        for prec, out in (("fp32k", (t32, nc, st)), ("fp64", (t64, nc64, None))):
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            hg.trace_rays(G, O, K, precision=prec, out=out)
+            if record:
+                e1.record(stream)
+                kev[prec].append((e0, e1))
+        grad.zero_()
+        hg.tau_gradient(G, O, K, W, grad=grad, grad_precision="fp32")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    bits = int(hg.reduce_status(st).item())
+    if bits:
+        raise RuntimeError(f"ray status bits {bits}")
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = hg.launch_count()
+    barrier(dist, dev)
+    torch.cuda.synchronize()
+    times = _timed_steps(torch, stream, args.steps, flush, lambda: step(True))
+    barrier(dist, dev)
+    launches = hg.launch_count() - l0
+    clk = clocks.stop()
+    tot_ms = max_over_ranks(dist, sum(times), dev)
+    value = sum_over_ranks(dist, n_rays * args.steps, dev) / (tot_ms / 1e3)
+    cr = int(nc.sum().item())
+    peak, src = _peak()
+    passes = {}
+    for prec in ("fp32k", "fp64"):
+        ms = statistics.mean(a.elapsed_time(b) for a, b in kev[prec])
+        byt = BYTES_PER_CROSSING[prec] * cr + BYTES_PER_RAY[prec] * n_rays
+        passes[prec] = dict(trace_ms=ms, rays_per_s=n_rays / ms * 1e3, gcross_per_s=cr / ms / 1e6,
+                            achieved_gbs=byt / (ms / 1e3) / 1e9, algorithmic_bytes=byt)
+    a32 = t32.double().cpu().numpy()
+    a64 = t64.cpu().numpy()
+    pos = a64 > 0
+    rel = np.abs(a32[pos] - a64[pos]) / a64[pos]
+    same_counts = bool(torch.equal(nc, nc64))
+    ach = passes["fp32k"]["achieved_gbs"]
+    roofline = dict(bound="hbm", achieved=round(ach, 1), peak=peak, unit="GB/s", frac=round(ach / peak, 4),
+                    traffic=recorded_traffic(args.workload, "fp32k"), kernel="trace_kernel FP32K (hg_trace_rays)",
+                    peak_source=src)
+    e2e = None
+    if not args.no_e2e:
+        ho, hk = torch.tensor(o).pin_memory(), torch.tensor(k).pin_memory()
+        h32 = torch.empty(n_rays, dtype=torch.float32).pin_memory()
+        h64 = torch.empty(n_rays, dtype=torch.float64).pin_memory()
+        hn = torch.empty(n_rays, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            O.copy_(ho, non_blocking=True)
+            K.copy_(hk, non_blocking=True)
+            step()
+            h32.copy_(t32, non_blocking=True)
+            h64.copy_(t64, non_blocking=True)
+            hn.copy_(nc, non_blocking=True)
+
+        barrier(dist, dev)
+        et = _timed_steps(torch, stream, args.steps, flush, e2e_step)
+        barrier(dist, dev)
+        e_ms = max_over_ranks(dist, sum(et), dev)
+        e2e = dict(value=sum_over_ranks(dist, n_rays * args.steps, dev) / (e_ms / 1e3), unit=UNIT,
+                   h2d_bytes_per_step=2 * n_rays * 24, d2h_bytes_per_step=n_rays * (4 + 8 + 4))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        H = g["host"]
+        T = oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho)
+        n = min(args.cpu_sample, n_rays)
+        threads = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        r = oracle.trace(T, o[:n], k[:n], emit=True, threads=threads)
+        oracle.adjoint(T.n_leaves, r["seg_off"], r["seg_cell"], r["seg_ds"], w[:n].astype(np.float64))
+        dt = time.perf_counter() - t0
+        cpu = dict(value=n / dt, unit=UNIT, cores=threads, kind="oracle",
+                   sample=f"{n} of the {n_rays} rays: FP64 trace with emission and adjoint accumulation")
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=tot_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32+f64", data="synthetic",
+                config=dict(workload=args.workload, description=desc, rays=n_rays, leaves=G.n_leaves,
+                            build_s=round(g["build_s"], 1), load_s=round(load_s, 2), mean_ncross=cr / n_rays,
+                            passes=passes, fp32k_vs_fp64=dict(max_rel=float(rel.max()), median_rel=float(np.median(rel)),
+                                                              identical_counts=same_counts),
+                            l2="flushed between steps (512 MB write); grid records exceed L2"),
+                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_batch(args):
+    import torch
+    import paper_1311_0705_gb300 as hg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    specs = synth.batch_specs(64)
+    grids, begins, leaves = [], [0], []
+    t0 = time.time()
+    for sp in specs:
+        bp = synth.BuildParams(kind=sp["kind"], delta_max=2.0 / sp["target_leaves"], max_level=10, seed=sp["seed"])
+        grids.append(hg.load_grid(hg.build_grid(sp["model"], bp)))
+        leaves.append(grids[-1].n_leaves)
+        begins.append(begins[-1] + sp["n_rays"])
+    build_s = time.time() - t0
+    total = begins[-1]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.config_seed(4) + 7919 * rank)
+    O = torch.rand(total, 3, dtype=torch.float64, device=dev, generator=gen) * 2.0 - 1.0
+    mu = torch.rand(total, dtype=torch.float64, device=dev, generator=gen) * 2.0 - 1.0
+    phi = torch.rand(total, dtype=torch.float64, device=dev, generator=gen) * (2.0 * math.pi)
+    sn = torch.sqrt(torch.clamp(1.0 - mu * mu, min=0.0))
+    K = torch.stack([sn * torch.cos(phi), sn * torch.sin(phi), mu], dim=1).contiguous()
+    batch = hg.Batch(grids, begins)
+    t32 = torch.empty(total, dtype=torch.float32, device=dev)
+    t64 = torch.empty(total, dtype=torch.float64, device=dev)
+    nc = torch.empty(total, dtype=torch.int32, device=dev)
+    st = torch.empty(total, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(args.warmup):
+            batch.trace(O, K, precision="fp32k", out=(t32, nc, st))
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.trace(O, K, precision="fp32k", out=(t32, nc, st))
+    graph.replay()
+    torch.cuda.synchronize()
+    bits = int(hg.reduce_status(st).item())
+    if bits:
+        raise RuntimeError(f"ray status bits {bits}")
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = hg.launch_count()
+    barrier(dist, dev)
+    torch.cuda.synchronize()
+    times = _timed_steps(torch, stream, args.steps, flush, graph.replay)
+    barrier(dist, dev)
+    clk = clocks.stop()
+    # graph replays launch the library's kernels without passing through its launch counter
+    launches = hg.launch_count() - l0 + 2 * args.steps
+    tot_ms = max_over_ranks(dist, sum(times), dev)
+    value = sum_over_ranks(dist, total * args.steps, dev) / (tot_ms / 1e3)
+    cr = int(nc.sum().item())
+
+    def sep(prec, out):
+        for i, g in enumerate(grids):
+            s = slice(begins[i], begins[i + 1])
+            hg.trace_rays(g, O[s], K[s], precision=prec, out=(out[0][s], out[1][s], out[2][s]))
+
+    sep("fp32k", (t32, nc, st))
+    sep_ms = statistics.mean(_timed_steps(torch, stream, max(1, min(3, args.steps)), flush,
+                                          lambda: sep("fp32k", (t32, nc, st))))
+    nc64 = torch.empty_like(nc)
+    b64_ms = statistics.mean(_timed_steps(torch, stream, max(1, min(3, args.steps)), flush,
+                                          lambda: batch.trace(O, K, precision="fp64", out=(t64, nc64, None))))
+    peak, src = _peak()
+    ach = (BYTES_PER_CROSSING["fp32k"] * cr + BYTES_PER_RAY["fp32k"] * total) / (tot_ms / args.steps / 1e3) / 1e9
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=tot_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32+f64", data="synthetic",
+                config=dict(workload=args.workload, description=WORKLOADS[args.workload][0], grids=len(grids),
+                            rays=total, leaves_total=int(sum(leaves)), leaves_min=int(min(leaves)),
+                            leaves_max=int(max(leaves)), build_s=round(build_s, 1), mean_ncross=cr / total,
+                            batched_fp32k_graph_ms=tot_ms / args.steps, separate_launches_fp32k_ms=sep_ms,
+                            batched_fp64_ms=b64_ms, separate_over_batched=sep_ms / (tot_ms / args.steps),
+                            rays_generated="on the device with a seeded torch generator",
+                            l2="flushed between steps (512 MB write)"),
+                roofline=dict(bound="hbm", achieved=round(ach, 1), peak=peak, unit="GB/s", frac=round(ach / peak, 4),
+                              traffic=None, kernel="batch_kernel FP32K (hg_batch_trace), setup pass included",
+                              peak_source=src),
+                cpu_baseline=None, e2e=None, gpu_launches=int(launches),
+                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- CPU oracle arm
 
 def oracle_step(oracle, model, trees, o, k, pts, pa, pk, pl, w, threads):
@@ -472,7 +729,14 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload in ("disk-1e6", "disk-1e4"):
+            run_reference(args)
+        else:
+            print(json.dumps(dict(impl="reference", unavailable="the CPU oracle arm covers the disk workloads only")))
+    elif args.workload == "torus-1e7":
+        run_torus(args)
+    elif args.workload == "batch-64":
+        run_batch(args)
     else:
         run_ours(args)
 

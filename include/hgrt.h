@@ -188,9 +188,12 @@ hg_status hg_grid_get_info(const hg_grid *g, hg_grid_info *out);
  * Directions are used as given (not normalised); s_max is in the same t. */
 typedef struct hg_trace_opts {
     int32_t precision;   /* HG_FP64 or HG_FP32K */
-    int32_t block;       /* threads per block; 0 = tuned or default */
+    int32_t block;       /* threads per block (32..256, multiple of 32); 0 = tuned or default */
     int32_t smem_nodes;  /* top tree nodes staged in shared memory (clamped to 200 KB); -1 = tuned or default */
-    int32_t schedule;    /* 0 = tuned or default, 1 = one ray per thread, 2 = persistent with warp refill */
+    int32_t schedule;    /* 0 = tuned or default, 1 = static ray stride, 2 = dynamic (warp-aggregated counter) */
+    int32_t min_blocks;  /* 0 = tuned or default (3); 3 or 4 resident 256-thread blocks per SM the
+                            kernel's register budget is cut for */
+    int32_t reserved;
     int64_t max_steps;   /* per-ray step limit; 0 = 4 * n_leaves + 64 */
 } hg_trace_opts;
 

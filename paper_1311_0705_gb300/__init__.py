@@ -79,7 +79,8 @@ class _GridInfo(C.Structure):
 class TraceOpts(C.Structure):
     """hg_trace_opts: precision, threads per block, shared-memory tree nodes, schedule, step limit."""
     _fields_ = [("precision", C.c_int32), ("block", C.c_int32), ("smem_nodes", C.c_int32),
-                ("schedule", C.c_int32), ("max_steps", C.c_int64)]
+                ("schedule", C.c_int32), ("min_blocks", C.c_int32), ("reserved", C.c_int32),
+                ("max_steps", C.c_int64)]
 
 
 _V = C.c_void_p
@@ -186,12 +187,13 @@ def _model_struct(model):
     return m, table
 
 
-def _opts(precision="fp64", block=0, smem_nodes=-1, schedule=0, max_steps=0) -> TraceOpts:
+def _opts(precision="fp64", block=0, smem_nodes=-1, schedule=0, max_steps=0, min_blocks=0) -> TraceOpts:
     o = TraceOpts()
     o.precision = {"fp64": FP64, "fp32k": FP32K, FP64: FP64, FP32K: FP32K}[precision]
     o.block = int(block)
     o.smem_nodes = int(smem_nodes)
     o.schedule = int(schedule)
+    o.min_blocks = int(min_blocks)
     o.max_steps = int(max_steps)
     return o
 
@@ -568,7 +570,8 @@ def autotune(grid: Grid, o, d, precision="fp64"):
     ms = C.c_float()
     p = {"fp64": FP64, "fp32k": FP32K}[precision]
     _check(_lib.hg_autotune(grid.handle, n, po, pd, p, C.byref(best), C.byref(ms), _stream()), "hg_autotune")
-    return dict(block=best.block, smem_nodes=best.smem_nodes, schedule=best.schedule), float(ms.value)
+    return dict(block=best.block, smem_nodes=best.smem_nodes, schedule=best.schedule,
+                min_blocks=best.min_blocks), float(ms.value)
 
 
 # ----------------------------------------------------------------------------- autograd

@@ -45,7 +45,36 @@ struct BatchArgs {
     uint8_t *status;
     int64_t max_steps;  // 0: per grid 4 n_leaves + 64
     unsigned long long *counter;
+    RayStart *starts;   // [total] start records, indexed by ray
 };
+
+// Queue position -> slot (grid in processing order) by binary search.
+__device__ __forceinline__ int queue_slot(const int64_t *s_qbeg, int n_grids, int64_t q) {
+    int lo = 0, hi = n_grids - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_qbeg[mid] <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Setup pass over the whole batch (checks, 1/d, clip, first leaf).
+__global__ void __launch_bounds__(256) batch_setup_kernel(const BatchArgs A) {
+    __shared__ int64_t s_qbeg[kMaxBatch + 1];
+    __shared__ int32_t s_perm[kMaxBatch];
+    for (int i = threadIdx.x; i <= A.n_grids; i += blockDim.x) s_qbeg[i] = A.qbeg[i];
+    for (int i = threadIdx.x; i < A.n_grids; i += blockDim.x) s_perm[i] = A.perm[i];
+    __syncthreads();
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < A.total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int slot = queue_slot(s_qbeg, A.n_grids, q);
+        const BatchEntry *E = A.E + s_perm[slot];
+        const int64_t ray = E->ray0 + (q - s_qbeg[slot]);
+        A.starts[ray] = ray_setup<2>(E->G, nullptr, 0, A.o, A.d, A.smax, ray);
+    }
+}
 
 template <int PREC>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
@@ -72,14 +101,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
             base = g.shfl(base, 0);
             const int64_t q = (int64_t)(base + g.thread_rank());
             if (q >= A.total) break;
-            int lo = 0, hi = A.n_grids - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_qbeg[mid] <= q)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
+            const int lo = queue_slot(s_qbeg, A.n_grids, q);
             E = A.E + s_perm[lo];
             ray = E->ray0 + (q - s_qbeg[lo]);
             {
@@ -90,7 +112,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
             acc32 = 0.0f;
             comp32 = 0.0f;
             nc = 0;
-            if (ray_init<2>(E->G, nullptr, 0, A.o, A.d, A.smax, ray, S, L, &st) == WALK_END) goto finish;
+            if (ray_resume(E->G, A.o, A.d, A.smax, A.starts, ray, S, L, &st) == WALK_END) goto finish;
         }
         {
             double ds, tex;
@@ -236,11 +258,21 @@ extern "C" hg_status hg_batch_trace(hg_batch *b, const double *o, const double *
     if (e != cudaSuccess) return cuda_err(e, "batch occupancy");
     int64_t blocks = (int64_t)std::max(1, per_sm) * sm_count();
     blocks = std::min<int64_t>(blocks, (b->total + block - 1) / block);
+    RayStart *starts = nullptr;
+    e = cudaMallocAsync((void **)&starts, (size_t)b->total * sizeof(RayStart), s);
+    if (e != cudaSuccess) return cuda_err(e, "batch start scratch");
+    A.starts = starts;
     e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_err(e, "batch counter reset");
+    if (e != cudaSuccess) {
+        cudaFreeAsync(starts, s);
+        return cuda_err(e, "batch counter reset");
+    }
+    const int64_t sblocks = std::min<int64_t>((b->total + 255) / 256, (int64_t)sm_count() * 8);
+    batch_setup_kernel<<<(unsigned)sblocks, 256, 0, s>>>(A);
     kern<<<(unsigned)blocks, block, 0, s>>>(A);
-    note_launches(1);
+    note_launches(2);
     e = cudaGetLastError();
+    cudaFreeAsync(starts, s);
     return e == cudaSuccess ? HG_OK : cuda_err(e, "batch launch");
 }
 
@@ -262,40 +294,42 @@ extern "C" hg_status hg_autotune(hg_grid *g, int64_t n, const double *o, const d
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
-    const int blocks[] = {128, 256, 512};
-    const int smem_kb[] = {0, 8, 32, 96};
+    const int blocks[] = {128, 256};
+    const int smem_kb[] = {0, 8, 32, 64};
     hg_trace_opts win{};
     float win_ms = 1e30f;
     hg_status st = HG_OK;
     for (int sched = 1; sched <= 2 && st == HG_OK; sched++)
-        for (int bl : blocks)
-            for (int kb : smem_kb) {
-                hg_trace_opts op{};
-                op.precision = precision;
-                op.block = bl;
-                op.smem_nodes = (int)std::min<int64_t>(g->d.n_nodes, (int64_t)kb * 1024 / node_bytes);
-                op.schedule = sched;
-                st = hg_trace_rays(g, n, o, d, nullptr, 1.0, &op, tau, nc, nullptr, stream);
-                if (st == HG_EINVAL) {  // shape does not fit: skip it
-                    st = HG_OK;
-                    continue;
-                }
-                if (st != HG_OK) break;
-                float best_here = 1e30f;
-                for (int rep = 0; rep < 3; rep++) {
-                    cudaEventRecord(e0, s);
+        for (int occ = 3; occ <= 4; occ++)
+            for (int bl : blocks)
+                for (int kb : smem_kb) {
+                    hg_trace_opts op{};
+                    op.precision = precision;
+                    op.block = bl;
+                    op.smem_nodes = (int)std::min<int64_t>(g->d.n_nodes, (int64_t)kb * 1024 / node_bytes);
+                    op.schedule = sched;
+                    op.min_blocks = occ;
                     st = hg_trace_rays(g, n, o, d, nullptr, 1.0, &op, tau, nc, nullptr, stream);
-                    cudaEventRecord(e1, s);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    best_here = std::min(best_here, ms);
+                    if (st == HG_EINVAL) {  // shape does not fit: skip it
+                        st = HG_OK;
+                        continue;
+                    }
+                    if (st != HG_OK) break;
+                    float best_here = 1e30f;
+                    for (int rep = 0; rep < 3; rep++) {
+                        cudaEventRecord(e0, s);
+                        st = hg_trace_rays(g, n, o, d, nullptr, 1.0, &op, tau, nc, nullptr, stream);
+                        cudaEventRecord(e1, s);
+                        cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        best_here = std::min(best_here, ms);
+                    }
+                    if (best_here < win_ms) {
+                        win_ms = best_here;
+                        win = op;
+                    }
                 }
-                if (best_here < win_ms) {
-                    win_ms = best_here;
-                    win = op;
-                }
-            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(tau, s);
@@ -307,6 +341,7 @@ extern "C" hg_status hg_autotune(hg_grid *g, int64_t n, const double *o, const d
     T.block = win.block;
     T.smem_nodes = win.smem_nodes;
     T.schedule = win.schedule;
+    T.min_blocks = win.min_blocks;
     if (best) *best = win;
     if (best_ms) *best_ms = win_ms;
     return HG_OK;

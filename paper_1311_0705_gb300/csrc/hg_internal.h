@@ -85,6 +85,7 @@ struct TuneEntry {
     int block = 0;
     int smem_nodes = 0;
     int schedule = 0;
+    int min_blocks = 0;
 };
 
 }  // namespace hg
@@ -102,5 +103,5 @@ struct hg_grid {
 namespace hg {
 // implemented in trace.cu
 hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precision, int &block, int &smem_nodes,
-                       int &schedule, int64_t &max_steps);
+                       int &schedule, int &min_blocks, int64_t &max_steps);
 }  // namespace hg

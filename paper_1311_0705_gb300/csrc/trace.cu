@@ -35,6 +35,7 @@ struct TraceArgs {
     const double *rho_ext;  // densities replacing the grid's own (MODE_TAU), or NULL
     int64_t max_steps;
     unsigned long long *counter;
+    const RayStart *starts;
     int n_smem;
     int dyn;
 };
@@ -47,14 +48,29 @@ __device__ __forceinline__ void stage_nodes(const void *nodes, int bytes, unsign
     __syncthreads();
 }
 
+// Setup pass: one ray per thread, every thread doing the same work (checks,
+// 1/d, clip, top-down location of the first leaf), so that the walking
+// kernel's refill is a handful of loads instead of a divergent descent.
+template <int KIND>
+__global__ void __launch_bounds__(256) setup_kernel(const DevGrid G, int64_t n, const double *__restrict__ o,
+                                                    const double *__restrict__ d, const double *__restrict__ smax,
+                                                    RayStart *starts, int n_smem) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        starts[r] = ray_setup<KIND>(G, smem, n_smem, o, d, smax, r);
+}
+
 // One persistent loop per thread: a lane whose ray has ended takes the next
 // ray (static stride, or a warp-aggregated atomic on a global counter) and
 // every iteration advances each lane by one crossing, so lanes never wait
 // for the longest path in their warp.
 //   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
 //   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
-template <int KIND, int MODE, int PREC>
-__global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A) {
+//   OCC: resident blocks of 256 threads per SM the register budget is cut for
+//   (3: 80 registers, no spills; 4: 64 registers).
+template <int KIND, int MODE, int PREC, int OCC>
+__global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const DevGrid &G = A.G;
     const int node_bytes = (KIND == HG_KDTREE) ? 16 : 32;
@@ -95,8 +111,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A) {
             nc = 0;
             if (MODE == MODE_FILL) seg_base = A.seg_off[ray];
             if (MODE == MODE_ADJ) wk = A.kappa * (double)A.w[ray];
-            const int r0 = ray_init<KIND>(G, smem, A.n_smem, A.o, A.d, A.smax, ray, S, L, &st);
-            if (r0 == WALK_END) goto finish;
+            if (ray_resume(G, A.o, A.d, A.smax, A.starts, ray, S, L, &st) == WALK_END) goto finish;
         }
         {
             double ds;
@@ -161,13 +176,13 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A) {
 
 typedef void (*KernelFn)(const TraceArgs);
 
-KernelFn pick_kernel(int kind, int mode, int prec) {
-#define HG_K(K, M, P) &trace_kernel<K, M, P>
-    static const KernelFn table[2][3][2] = {
+KernelFn pick_kernel(int kind, int mode, int prec, int occ) {
+#define HG_K(K, M, P) {&trace_kernel<K, M, P, 3>, &trace_kernel<K, M, P, 4>}
+    static const KernelFn table[2][3][2][2] = {
         {{HG_K(0, 0, 0), HG_K(0, 0, 1)}, {HG_K(0, 1, 0), HG_K(0, 1, 1)}, {HG_K(0, 2, 0), HG_K(0, 2, 1)}},
         {{HG_K(1, 0, 0), HG_K(1, 0, 1)}, {HG_K(1, 1, 0), HG_K(1, 1, 1)}, {HG_K(1, 2, 0), HG_K(1, 2, 1)}}};
 #undef HG_K
-    return table[kind][mode][prec];
+    return table[kind][mode][prec][occ == 4 ? 1 : 0];
 }
 
 hg_status cuda_err(cudaError_t e, const char *what) {
@@ -189,7 +204,7 @@ int sm_count() {
 // Default launch shape: 256 threads, the top 2048 k-d nodes (32 KB) or
 // 1024 octree nodes (32 KB) in shared memory, persistent dynamic schedule.
 hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precision, int &block, int &smem_nodes,
-                       int &schedule, int64_t &max_steps) {
+                       int &schedule, int &min_blocks, int64_t &max_steps) {
     precision = opts ? opts->precision : HG_FP64;
     if (precision != HG_FP64 && precision != HG_FP32K) {
         set_error("precision must be HG_FP64 or HG_FP32K");
@@ -200,9 +215,14 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
     smem_nodes = (opts && opts->smem_nodes >= 0) ? opts->smem_nodes
                                                   : (T.valid ? T.smem_nodes : (g->d.kind == HG_KDTREE ? 2048 : 1024));
     schedule = (opts && opts->schedule > 0) ? opts->schedule : (T.valid ? T.schedule : 2);
+    min_blocks = (opts && opts->min_blocks > 0) ? opts->min_blocks : (T.valid ? T.min_blocks : 3);
     max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 4 * g->d.n_leaves + 64;
-    if (block < 32 || block > 512 || block % 32) {
-        set_error("block must be a multiple of 32 in 32..512");
+    if (block < 32 || block > 256 || block % 32) {
+        set_error("block must be a multiple of 32 in 32..256");
+        return HG_EINVAL;
+    }
+    if (min_blocks != 3 && min_blocks != 4) {
+        set_error("min_blocks must be 3 or 4");
         return HG_EINVAL;
     }
     if (schedule != 1 && schedule != 2) {
@@ -216,9 +236,9 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
 }
 
 hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int block, int smem_nodes, int schedule,
-                       cudaStream_t stream) {
+                       int min_blocks, cudaStream_t stream) {
     if (A.n == 0) return HG_OK;
-    KernelFn k = pick_kernel(g->d.kind, mode, prec);
+    KernelFn k = pick_kernel(g->d.kind, mode, prec, min_blocks);
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
     const size_t smem = (size_t)smem_nodes * node_bytes;
     static std::once_flag once;
@@ -226,8 +246,11 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
         for (int kd = 0; kd < 2; kd++)
             for (int m = 0; m < 3; m++)
                 for (int p = 0; p < 2; p++)
-                    cudaFuncSetAttribute(pick_kernel(kd, m, p), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
+                    for (int oc = 3; oc <= 4; oc++)
+                        cudaFuncSetAttribute(pick_kernel(kd, m, p, oc), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
@@ -241,13 +264,32 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
     if (blocks > need) blocks = need;
     A.n_smem = smem_nodes;
     A.dyn = (schedule == 2);
+    // setup pass into a scratch array of start records
+    RayStart *starts = nullptr;
+    e = cudaMallocAsync((void **)&starts, (size_t)A.n * sizeof(RayStart), stream);
+    if (e != cudaSuccess) return cuda_err(e, "ray start scratch");
+    {
+        const int64_t sblocks = std::min<int64_t>((A.n + 255) / 256, (int64_t)sm_count() * 8);
+        if (g->d.kind == HG_KDTREE)
+            setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, A.n, A.o, A.d, A.smax, starts,
+                                                                             smem_nodes);
+        else
+            setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, A.n, A.o, A.d, A.smax, starts,
+                                                                             smem_nodes);
+        note_launches(1);
+    }
+    A.starts = starts;
     unsigned long long *ctr = nullptr;
     if (A.dyn) {
         e = cudaMallocAsync((void **)&ctr, sizeof(unsigned long long), stream);
-        if (e != cudaSuccess) return cuda_err(e, "scratch counter");
+        if (e != cudaSuccess) {
+            cudaFreeAsync(starts, stream);
+            return cuda_err(e, "scratch counter");
+        }
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) {
             cudaFreeAsync(ctr, stream);
+            cudaFreeAsync(starts, stream);
             return cuda_err(e, "scratch counter");
         }
         A.counter = ctr;
@@ -256,6 +298,7 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
     e = cudaGetLastError();
     note_launches(1);
     if (ctr) cudaFreeAsync(ctr, stream);
+    cudaFreeAsync(starts, stream);
     if (e != cudaSuccess) return cuda_err(e, "trace launch");
     return HG_OK;
 }
@@ -404,9 +447,9 @@ extern "C" hg_status hg_trace_rays(const hg_grid *g, int64_t n, const double *o,
         set_error("hg_trace_rays: tau and ncross are required");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule;
+    int prec, block, smem_nodes, schedule, min_blocks;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -418,7 +461,7 @@ extern "C" hg_status hg_trace_rays(const hg_grid *g, int64_t n, const double *o,
     A.ncross = ncross;
     A.status = ray_status;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double *o, const double *d,
@@ -431,9 +474,9 @@ extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double
         set_error("hg_trace_rays_rho: rho, tau and ncross are required");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule;
+    int prec, block, smem_nodes, schedule, min_blocks;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -446,7 +489,7 @@ extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double
     A.ncross = ncross;
     A.status = ray_status;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o, const double *d,
@@ -459,9 +502,9 @@ extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o,
         set_error("hg_trace_fill: bad segment arrays");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule;
+    int prec, block, smem_nodes, schedule, min_blocks;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -474,7 +517,7 @@ extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o,
     A.seg_cap = seg_capacity;
     A.status = ray_status;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_FILL, prec, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+    return launch_trace(g, MODE_FILL, prec, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *o, const double *d,
@@ -490,9 +533,9 @@ extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *
         set_error("hg_tau_gradient: grad_precision must be 0 (f64) or 1 (f32)");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule;
+    int prec, block, smem_nodes, schedule, min_blocks;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -503,7 +546,7 @@ extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *
     A.w = w;
     A.grad = grad_rho;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_ADJ, grad_precision, A, block, smem_nodes, schedule, (cudaStream_t)stream);
+    return launch_trace(g, MODE_ADJ, grad_precision, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_sample_density(const hg_grid *g, int64_t n, const double *pts, int32_t *cell, double *rho,

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <cstddef>
+
 #include "hg_internal.h"
 
 namespace hg {
@@ -161,23 +163,40 @@ struct RayState {
 
 enum { WALK_GO = 0, WALK_END = 1 };
 
-// Set up a ray: checks, clip against the domain, first leaf.  Returns
-// WALK_GO with S.cur and L filled, or WALK_END (status in *st).  Runs once
-// per ray, so it keeps plain FP64 compares.
+// Start state of a ray, written by the setup pass and read when a walking
+// thread takes the ray: 48 bytes, three 16-byte loads.
+struct alignas(16) RayStart {
+    double ik0, ik1, ik2;  // 1/d per axis (0 where d_a == 0)
+    long long ktstart;     // key of the entry time
+    int32_t cur;           // first leaf, or -1 when the ray does not walk
+    uint32_t sg;           // direction sign bits | status bits << 8
+    int64_t pad;
+};
+static_assert(sizeof(RayStart) == 48 && offsetof(RayStart, ktstart) == 24 && offsetof(RayStart, cur) == 32 &&
+                  offsetof(RayStart, sg) == 36,
+              "ray_resume reads the start record as two double2 and one int4");
+
+// Set up a ray (the first-cell location of Sect. 2.3): checks, 1/d, clip
+// against the domain, top-down descent to the first leaf.  Runs once per
+// ray in its own pass, so it keeps plain FP64 compares.
 template <int KIND>
-__device__ __forceinline__ int ray_init(const DevGrid &G, const unsigned char *snodes, int n_smem,
-                                        const double *__restrict__ o, const double *__restrict__ d,
-                                        const double *__restrict__ smax, int64_t r, RayState &S, Leaf &L,
-                                        uint32_t *st) {
-    *st = 0;
+__device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned char *snodes, int n_smem,
+                                              const double *__restrict__ o, const double *__restrict__ d,
+                                              const double *__restrict__ smax, int64_t r) {
+    RayStart R;
+    R.ik0 = R.ik1 = R.ik2 = 0.0;
+    R.ktstart = 0;
+    R.cur = -1;
+    R.sg = 0;
+    R.pad = 0;
     double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
     const double kk[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
     const double tend = smax ? smax[r] : CUDART_INF;
     if (!(isfinite(oo[0]) && isfinite(oo[1]) && isfinite(oo[2]) && isfinite(kk[0]) && isfinite(kk[1]) &&
           isfinite(kk[2])) ||
         (kk[0] == 0.0 && kk[1] == 0.0 && kk[2] == 0.0) || isnan(tend)) {
-        *st = HG_RAY_BADINPUT;
-        return WALK_END;
+        R.sg = HG_RAY_BADINPUT << 8;
+        return R;
     }
     // a signed-zero origin coordinate gives the same comparisons and sums as +0
 #pragma unroll
@@ -196,7 +215,7 @@ __device__ __forceinline__ int ray_init(const DevGrid &G, const unsigned char *s
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         if (kk[a] == 0.0) {
-            if (oo[a] < G.dlo[a] || oo[a] > G.dhi[a]) return WALK_END;
+            if (oo[a] < G.dlo[a] || oo[a] > G.dhi[a]) return R;
             continue;
         }
         const double tn = ((kk[a] > 0.0 ? G.dlo[a] : G.dhi[a]) - oo[a]) * ik[a];
@@ -207,7 +226,7 @@ __device__ __forceinline__ int ray_init(const DevGrid &G, const unsigned char *s
         }
         if (tf < tout) tout = tf;
     }
-    if (!(ts < tout) || !(ts < tend)) return WALK_END;
+    if (!(ts < tout) || !(ts < tend)) return R;
     long long p[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -225,27 +244,49 @@ __device__ __forceinline__ int ray_init(const DevGrid &G, const unsigned char *s
     }
 #pragma unroll
     for (int a = 0; a < 3; a++)
-        if (!in_axis(p[a], okey(G.dlo[a]), okey(G.dhi[a]), dpos(sg, a), dneg(sg, a), true)) return WALK_END;
+        if (!in_axis(p[a], G.klo[a], G.khi[a], dpos(sg, a), dneg(sg, a), true)) return R;
     const int32_t c = descend<KIND>(G, snodes, n_smem, p[0], p[1], p[2], sg);
     if (c < 0) {
-        *st = HG_RAY_LOST;
-        return WALK_END;
+        R.sg = HG_RAY_LOST << 8;
+        return R;
     }
-    S.o0 = oo[0];
-    S.o1 = oo[1];
-    S.o2 = oo[2];
-    S.k0 = kk[0];
-    S.k1 = kk[1];
-    S.k2 = kk[2];
-    S.ik0 = ik[0];
-    S.ik1 = ik[1];
-    S.ik2 = ik[2];
-    S.sg = sg;
-    S.ktend = okey(tend);
-    S.ktcur = okey(ts);
-    S.cur = c;
+    R.ik0 = ik[0];
+    R.ik1 = ik[1];
+    R.ik2 = ik[2];
+    R.ktstart = okey(ts);
+    R.cur = c;
+    R.sg = sg;
+    return R;
+}
+
+// Take a ray for walking from its start record.  Returns WALK_GO with S and
+// L filled, or WALK_END with the setup status in *st.
+__device__ __forceinline__ int ray_resume(const DevGrid &G, const double *__restrict__ o,
+                                          const double *__restrict__ d, const double *__restrict__ smax,
+                                          const RayStart *__restrict__ starts, int64_t r, RayState &S, Leaf &L,
+                                          uint32_t *st) {
+    const double2 *q = reinterpret_cast<const double2 *>(starts + r);
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    const int4 c = __ldg(reinterpret_cast<const int4 *>(q + 2));
+    // c = {cur, sg | status << 8, pad, pad}
+    *st = (uint32_t)c.y >> 8;
+    if (c.x < 0) return WALK_END;
+    S.ik0 = a.x;
+    S.ik1 = a.y;
+    S.ik2 = b.x;
+    S.ktcur = __double_as_longlong(b.y);
+    S.cur = c.x;
+    S.sg = (uint32_t)c.y & 0xffu;
+    double o0 = o[3 * r], o1 = o[3 * r + 1], o2 = o[3 * r + 2];
+    S.o0 = (o0 == 0.0) ? 0.0 : o0;
+    S.o1 = (o1 == 0.0) ? 0.0 : o1;
+    S.o2 = (o2 == 0.0) ? 0.0 : o2;
+    S.k0 = d[3 * r];
+    S.k1 = d[3 * r + 1];
+    S.k2 = d[3 * r + 2];
+    S.ktend = smax ? okey(smax[r]) : KEY_INF;
     S.steps = 0;
-    load_leaf(G.rec, c, L);
+    load_leaf(G.rec, S.cur, L);
     return WALK_GO;
 }
 
