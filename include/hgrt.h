@@ -211,6 +211,30 @@ hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double *o, const 
                             double kappa, const double *rho, const hg_trace_opts *opts, void *tau,
                             int32_t *ncross, uint8_t *ray_status, hg_stream stream);
 
+/* Allocation-free optical-depth pass (the paper has no counterpart: this is
+ * an interface of this library only).  Some callers cannot allocate device
+ * memory at the time they trace -- code running inside a stream capture
+ * whose owner forbids allocation nodes, real-time loops that must never
+ * enter an allocator, hosts that give the library a fixed memory budget.
+ * This call computes exactly what hg_trace_rays computes (same arguments,
+ * same results), but takes its scratch -- one 48-byte start record per ray
+ * and a work counter -- from a fixed array compiled into the library, and
+ * calls no cudaMalloc, cudaFree or other allocator.
+ *   - n must not exceed HG_NOALLOC_MAX_RAYS; a larger n returns HG_EINVAL
+ *     before anything is launched (split the batch, or use hg_trace_rays).
+ *   - Every GPU that loads the library holds the array (about 12.6 MB)
+ *     until the process exits.
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; calls
+ *     whose work overlaps on the GPU (other streams, other host threads)
+ *     race and give wrong results, so serialise them. */
+#define HG_NOALLOC_MAX_RAYS 262144
+hg_status hg_trace_rays_noalloc(const hg_grid *g, int64_t n, const double *o, const double *d,
+                                const double *s_max, double kappa, const hg_trace_opts *opts, void *tau,
+                                int32_t *ncross, uint8_t *ray_status, hg_stream stream);
+
 /* Exclusive scan: seg_off[0] = 0, seg_off[i+1] = seg_off[i] + count[i]
  * (dev i32[n] -> dev i64[n+1]). */
 hg_status hg_scan_offsets(int64_t n, const int32_t *count, int64_t *seg_off, hg_stream stream);

@@ -29,6 +29,7 @@ RAY_STEPLIMIT = 1
 RAY_LOST = 2
 RAY_BADINPUT = 4
 RAY_OVERFLOW = 8
+NOALLOC_MAX_RAYS = 262144  # HG_NOALLOC_MAX_RAYS
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -95,6 +96,7 @@ _SIGS = {
     "hg_free_grid": (None, [_V]),
     "hg_grid_get_info": (_S, [_V, C.POINTER(_GridInfo)]),
     "hg_trace_rays": (_S, [_V, _I64, _V, _V, _V, C.c_double, C.POINTER(TraceOpts), _V, _V, _V, _V]),
+    "hg_trace_rays_noalloc": (_S, [_V, _I64, _V, _V, _V, C.c_double, C.POINTER(TraceOpts), _V, _V, _V, _V]),
     "hg_trace_rays_rho": (_S, [_V, _I64, _V, _V, _V, C.c_double, _V, C.POINTER(TraceOpts), _V, _V, _V, _V]),
     "hg_scan_offsets": (_S, [_I64, _V, _V, _V]),
     "hg_trace_fill": (_S, [_V, _I64, _V, _V, _V, C.POINTER(TraceOpts), _V, _V, _V, _I64, _V, _V]),
@@ -370,6 +372,27 @@ def trace_rays(grid: Grid, o, d, s_max=None, kappa: float = 1.0, precision="fp64
     _check(_lib.hg_trace_rays(grid.handle, n, po, pd, ps, float(kappa), C.byref(op), _dptr(tau, tdt, (n,), "tau"),
                               _dptr(nc, torch.int32, (n,), "ncross"), _dptr(st, torch.uint8, (n,), "status"),
                               _stream()), "hg_trace_rays")
+    return tau, nc, st
+
+
+def trace_rays_noalloc(grid: Grid, o, d, s_max=None, kappa: float = 1.0, precision="fp64", out=None,
+                       status: bool = True, **opt):
+    """hg_trace_rays_noalloc: as trace_rays, with the library's fixed scratch instead of
+    the allocator (for callers that cannot allocate device memory while they trace;
+    at most NOALLOC_MAX_RAYS rays per call, calls must not overlap on the GPU)."""
+    torch = _torch()
+    n, po, pd, ps = _rays(o, d, s_max)
+    op = _opts(precision, **opt)
+    tdt = torch.float64 if op.precision == FP64 else torch.float32
+    if out is None:
+        tau = torch.empty(n, dtype=tdt, device=o.device)
+        nc = torch.empty(n, dtype=torch.int32, device=o.device)
+        st = torch.empty(n, dtype=torch.uint8, device=o.device) if status else None
+    else:
+        tau, nc, st = out
+    _check(_lib.hg_trace_rays_noalloc(grid.handle, n, po, pd, ps, float(kappa), C.byref(op),
+                                      _dptr(tau, tdt, (n,), "tau"), _dptr(nc, torch.int32, (n,), "ncross"),
+                                      _dptr(st, torch.uint8, (n,), "status"), _stream()), "hg_trace_rays_noalloc")
     return tau, nc, st
 
 

@@ -26,6 +26,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = [
     ("trace.cu", True),
     ("batch.cu", True),
+    ("noalloc.cu", True),
     ("metrics.cu", False),
     ("grid.cpp", False),
     ("build.cpp", False),

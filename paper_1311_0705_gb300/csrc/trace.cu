@@ -627,3 +627,70 @@ extern "C" hg_status hg_sum_i32(int64_t n, const int32_t *x, int64_t *out, hg_st
     }
     return e == cudaSuccess ? HG_OK : cuda_err(e, "sum");
 }
+
+namespace hg {
+
+// Launch the FP64 / FP32K optical-depth pass with scratch the caller
+// provides (start records for n rays and a work counter) instead of the
+// stream-ordered allocator.  Used by the allocation-free entry point.
+hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, const double *d, const double *s_max,
+                              double kappa, const hg_trace_opts *opts, void *tau, int32_t *ncross,
+                              uint8_t *ray_status, RayStart *starts, unsigned long long *counter,
+                              cudaStream_t stream) {
+    hg_status st = check_rays(g, n, o, d);
+    if (st != HG_OK) return st;
+    if (n > 0 && (!tau || !ncross)) {
+        set_error("tau and ncross are required");
+        return HG_EINVAL;
+    }
+    int prec, block, smem_nodes, schedule, min_blocks;
+    int64_t max_steps;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
+    if (n == 0) return HG_OK;
+    TraceArgs A{};
+    A.G = g->d;
+    A.n = n;
+    A.o = o;
+    A.d = d;
+    A.smax = s_max;
+    A.kappa = kappa;
+    A.tau = tau;
+    A.ncross = ncross;
+    A.status = ray_status;
+    A.max_steps = max_steps;
+    A.n_smem = smem_nodes;
+    A.dyn = (schedule == 2);
+    A.starts = starts;
+    A.counter = counter;
+    KernelFn k = pick_kernel(g->d.kind, MODE_TAU, prec, min_blocks);
+    const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
+    const size_t smem = (size_t)smem_nodes * node_bytes;
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
+    if (e != cudaSuccess) return cuda_err(e, "occupancy query");
+    if (per_sm < 1) {
+        set_error("launch shape does not fit on an SM (block %d, %zu B shared)", block, smem);
+        return HG_EINVAL;
+    }
+    int64_t blocks = std::min<int64_t>((int64_t)per_sm * sm_count(), (n + block - 1) / block);
+    if (A.dyn) {
+        e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return cuda_err(e, "counter reset");
+    }
+    const int64_t sblocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    if (g->d.kind == HG_KDTREE)
+        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes);
+    else
+        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes);
+    k<<<(unsigned)blocks, block, smem, stream>>>(A);
+    note_launches(2);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "trace launch");
+}
+
+}  // namespace hg
