@@ -119,7 +119,7 @@ typedef struct hg_grid_desc {
     const int32_t *node_leaf;    /* [n_nodes], leaf id or -1; leaf ids follow list order */
     const double *leaf_rho;      /* [n_leaves] */
     const int64_t *nbr_off;      /* [6*n_leaves+1], list of wall w of leaf i = nbr_off[6i+w] .. nbr_off[6i+w+1] */
-    const int32_t *nbr_id;       /* [nbr_off[6*n_leaves]] */
+    const int32_t *nbr_id;       /* [nbr_off[6*n_leaves]]; may be NULL when that is 0 (a single leaf) */
 } hg_grid_desc;
 
 /* Extra per-node builder output (host arrays owned by the hg_host_grid). */

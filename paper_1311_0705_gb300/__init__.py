@@ -223,7 +223,7 @@ class HostGrid:
         self.leaf_rho = v(d.leaf_rho, (nl,))
         self.nbr_off = v(d.nbr_off, (6 * nl + 1,))
         n_nbr = int(self.nbr_off[-1])
-        self.nbr_id = v(d.nbr_id, (max(n_nbr, 1),))[:n_nbr]
+        self.nbr_id = v(d.nbr_id, (n_nbr,)) if n_nbr > 0 else np.zeros(0, np.int32)
         self.level = v(nd.level, (n, 3))
         self.index = v(nd.index, (n, 3))
         self.mass = v(nd.mass, (n,))

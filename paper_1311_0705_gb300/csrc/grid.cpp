@@ -167,7 +167,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
     *out = nullptr;
     const hg_grid_desc D = *desc;
     if ((D.kind != HG_OCTREE && D.kind != HG_KDTREE) || D.n_nodes < 1 || D.n_leaves < 1 || !D.node_lo ||
-        !D.node_hi || !D.child_first || !D.node_leaf || !D.leaf_rho || !D.nbr_off || !D.nbr_id) {
+        !D.node_hi || !D.child_first || !D.node_leaf || !D.leaf_rho || !D.nbr_off ||
+        (!D.nbr_id && D.nbr_off[6 * D.n_leaves] > 0)) {
         hg::set_error("hg_load_grid: incomplete description");
         return HG_EINVAL;
     }

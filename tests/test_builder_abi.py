@@ -174,3 +174,11 @@ def test_builder_rejects_bad_parameters():
     bp.max_nodes = 100
     with pytest.raises(hg.HgError, match="capacity"):
         hg.build_grid(synth.make_const(), bp)
+
+
+def test_single_leaf_grid_has_no_neighbor_entries():
+    # a root that no criterion splits (here delta = 1 <= delta_max) stays the only leaf; the same
+    # happens when all of a root's Monte Carlo samples miss a thin structure (Eq. 1 gives M = 0)
+    bp = synth.BuildParams(kind=0, delta_max=2.0, max_level=4)
+    H = hg.build_grid(synth.make_const(1.0), bp)
+    assert H.n_leaves == 1 and H.nbr_id.size == 0 and (H.nbr_off == 0).all()

@@ -380,3 +380,13 @@ def test_disk_1e6_leaves_1e6_rays(hg, disk_1e6, kind):
     # full sequences on a sample of rays, traced in the same launch shape as the benchmark
     sel = np.random.default_rng(kind).choice(o.shape[0], 20000, replace=False)
     _compare(hg, grid, tree, o[sel], k[sel])
+
+
+def test_single_leaf_grid(hg):
+    model = synth.make_const(2.0)
+    bp = synth.BuildParams(kind=1, delta_max=2.0, max_level=3)
+    grid = hg.load_grid(hg.build_grid(model, bp))
+    tree = oracle.build_tree(model, bp)
+    assert tree.n_leaves == 1
+    o, k = synth.emission_rays(4, 500)
+    _compare(hg, grid, tree, o, k)
