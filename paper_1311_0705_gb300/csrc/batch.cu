@@ -76,6 +76,29 @@ __global__ void __launch_bounds__(256) batch_setup_kernel(const BatchArgs A) {
     }
 }
 
+// Rays of the whole batch: queue positions from a warp-aggregated atomic
+// counter, mapped to (grid, ray) through the queue offsets in shared memory.
+struct BatchRays {
+    const BatchArgs *A;
+    const int64_t *s_qbeg;
+    const int32_t *s_perm;
+    __device__ __forceinline__ bool next(int64_t &ray, const DevGrid *&g, int32_t &ms) {
+        cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(A->counter, (unsigned long long)grp.size());
+        base = grp.shfl(base, 0);
+        const int64_t q = (int64_t)(base + grp.thread_rank());
+        if (q >= A->total) return false;
+        const int slot = queue_slot(s_qbeg, A->n_grids, q);
+        const BatchEntry *E = A->E + s_perm[slot];
+        ray = E->ray0 + (q - s_qbeg[slot]);
+        g = &E->G;
+        const int64_t m = A->max_steps > 0 ? A->max_steps : E->max_steps;
+        ms = (int32_t)(m < 0x7fffffff ? m : 0x7fffffff);
+        return true;
+    }
+};
+
 template <int PREC>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
     __shared__ int64_t s_qbeg[kMaxBatch + 1];
@@ -83,66 +106,17 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
     for (int i = threadIdx.x; i <= A.n_grids; i += blockDim.x) s_qbeg[i] = A.qbeg[i];
     for (int i = threadIdx.x; i < A.n_grids; i += blockDim.x) s_perm[i] = A.perm[i];
     __syncthreads();
-    const float kappa32 = (float)A.kappa;
-    int64_t ray = -1;
-    const BatchEntry *E = nullptr;
-    int32_t max_steps32 = 0;
-    RayState S;
-    Leaf L;
-    double acc = 0.0;
-    float acc32 = 0.0f, comp32 = 0.0f;
-    int32_t nc = 0;
-    uint32_t st = 0;
-    for (;;) {
-        if (ray < 0) {
-            cg::coalesced_group g = cg::coalesced_threads();
-            unsigned long long base = 0;
-            if (g.thread_rank() == 0) base = atomicAdd(A.counter, (unsigned long long)g.size());
-            base = g.shfl(base, 0);
-            const int64_t q = (int64_t)(base + g.thread_rank());
-            if (q >= A.total) break;
-            const int lo = queue_slot(s_qbeg, A.n_grids, q);
-            E = A.E + s_perm[lo];
-            ray = E->ray0 + (q - s_qbeg[lo]);
-            {
-                const int64_t ms = A.max_steps > 0 ? A.max_steps : E->max_steps;
-                max_steps32 = (int32_t)(ms < 0x7fffffff ? ms : 0x7fffffff);
-            }
-            acc = 0.0;
-            acc32 = 0.0f;
-            comp32 = 0.0f;
-            nc = 0;
-            if (ray_resume(E->G, A.o, A.d, A.smax, A.starts, ray, S, L, &st) == WALK_END) goto finish;
-        }
-        {
-            double ds, tex;
-            int ax;
-            const int r1 = ray_exit(max_steps32, S, L, &ds, &ax, &tex, &st);
-            if (ds != 0.0) {
-                if (PREC == HG_FP64) {
-                    acc = acc + L.rho * ds;
-                } else {
-                    const float kr = __fmul_rn(kappa32, L.rho32);
-                    const float y = __fsub_rn(__fmul_rn(kr, __double2float_rn(ds)), comp32);
-                    const float t = __fadd_rn(acc32, y);
-                    comp32 = __fsub_rn(__fsub_rn(t, acc32), y);
-                    acc32 = t;
-                }
-                nc++;
-            }
-            if (r1 == WALK_END) goto finish;
-            if (ray_advance<2>(E->G, nullptr, 0, S, L, ax, tex, &st) == WALK_END) goto finish;
-            continue;
-        }
-    finish:
-        if (PREC == HG_FP64)
-            static_cast<double *>(A.tau)[ray] = A.kappa * acc;
-        else
-            static_cast<float *>(A.tau)[ray] = acc32;
-        A.ncross[ray] = nc;
-        if (A.status) A.status[ray] = (uint8_t)st;
-        ray = -1;
-    }
+    BatchRays src{&A, s_qbeg, s_perm};
+    WalkIO io{};
+    io.o = A.o;
+    io.d = A.d;
+    io.smax = A.smax;
+    io.starts = A.starts;
+    io.kappa = A.kappa;
+    io.tau = A.tau;
+    io.ncross = A.ncross;
+    io.status = A.status;
+    walk_loop<2, MODE_TAU, PREC>(src, io, nullptr, 0);
 }
 
 }  // namespace hg

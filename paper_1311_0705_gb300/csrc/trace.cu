@@ -14,8 +14,6 @@ namespace cg = cooperative_groups;
 
 namespace hg {
 
-enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2 };
-
 struct TraceArgs {
     DevGrid G;
     int64_t n;
@@ -61,115 +59,68 @@ __global__ void __launch_bounds__(256) setup_kernel(const DevGrid G, int64_t n, 
         starts[r] = ray_setup<KIND>(G, smem, n_smem, o, d, smax, r);
 }
 
-// One persistent loop per thread: a lane whose ray has ended takes the next
-// ray (static stride, or a warp-aggregated atomic on a global counter) and
-// every iteration advances each lane by one crossing, so lanes never wait
-// for the longest path in their warp.
-//   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
-//   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
+// Rays of one grid for the walking loop: a static stride, or a
+// warp-aggregated atomic on a global counter.
+struct GridRays {
+    const DevGrid *G;
+    int64_t n;
+    int64_t cursor;
+    int64_t stride;
+    unsigned long long *counter;
+    int32_t max_steps;
+    bool dyn;
+    __device__ __forceinline__ bool next(int64_t &ray, const DevGrid *&g, int32_t &ms) {
+        g = G;
+        ms = max_steps;
+        if (dyn) {
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned long long base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(counter, (unsigned long long)grp.size());
+            base = grp.shfl(base, 0);
+            ray = (int64_t)(base + grp.thread_rank());
+        } else {
+            ray = cursor;
+            cursor += stride;
+        }
+        return ray < n;
+    }
+};
+
+// One persistent loop per thread (walk_loop): a lane whose ray has ended
+// takes the next one, and every iteration advances each lane by one record
+// load, so lanes never wait for the longest path in their warp.
 //   OCC: resident blocks of 256 threads per SM the register budget is cut for
-//   (3: 80 registers, no spills; 4: 64 registers).
+//   (3: 80 registers; 4: 64 registers).
 template <int KIND, int MODE, int PREC, int OCC>
 __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const DevGrid &G = A.G;
     const int node_bytes = (KIND == HG_KDTREE) ? 16 : 32;
-    stage_nodes(G.nodes, A.n_smem * node_bytes, smem);
-
-    int64_t next = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t ray = -1;
-    RayState S;
-    Leaf L;
-    double acc = 0.0;     // FP64 sum of rho*ds
-    float acc32 = 0.0f;   // FP32 Kahan sum
-    float comp32 = 0.0f;  // Kahan compensation
-    float kr32 = 0.0f;    // (float)kappa * rho32 of the current leaf
-    int32_t nc = 0;
-    int64_t seg_base = 0;
-    double wk = 0.0;  // kappa * w for the adjoint
-    uint32_t st = 0;
-    const float kappa32 = (float)A.kappa;
-    const int32_t max_steps32 = (int32_t)(A.max_steps < 0x7fffffff ? A.max_steps : 0x7fffffff);
-
-    for (;;) {
-        if (ray < 0) {
-            if (A.dyn) {
-                cg::coalesced_group g = cg::coalesced_threads();
-                unsigned long long base = 0;
-                if (g.thread_rank() == 0) base = atomicAdd(A.counter, (unsigned long long)g.size());
-                base = g.shfl(base, 0);
-                ray = (int64_t)(base + g.thread_rank());
-            } else {
-                ray = next;
-                next += stride;
-            }
-            if (ray >= A.n) break;
-            acc = 0.0;
-            acc32 = 0.0f;
-            comp32 = 0.0f;
-            nc = 0;
-            if (MODE == MODE_FILL) seg_base = A.seg_off[ray];
-            if (MODE == MODE_ADJ) wk = A.kappa * (double)A.w[ray];
-            if (ray_resume(G, A.o, A.d, A.smax, A.starts, ray, S, L, &st) == WALK_END) goto finish;
-        }
-        {
-            double ds;
-            int ax;
-            double tex;
-            const int r1 = ray_exit(max_steps32, S, L, &ds, &ax, &tex, &st);
-            if (ds != 0.0) {
-                if (MODE == MODE_TAU) {
-                    if (PREC == HG_FP64) {
-                        const double rho = A.rho_ext ? __ldg(A.rho_ext + S.cur) : L.rho;
-                        acc = acc + rho * ds;
-                    } else {
-                        const float rho32 = A.rho_ext ? __double2float_rn(__ldg(A.rho_ext + S.cur)) : L.rho32;
-                        kr32 = __fmul_rn(kappa32, rho32);
-                        const float y = __fsub_rn(__fmul_rn(kr32, __double2float_rn(ds)), comp32);
-                        const float t = __fadd_rn(acc32, y);
-                        comp32 = __fsub_rn(__fsub_rn(t, acc32), y);
-                        acc32 = t;
-                    }
-                } else if (MODE == MODE_FILL) {
-                    const int64_t idx = seg_base + nc;
-                    if (idx >= A.seg_cap) {
-                        st |= HG_RAY_OVERFLOW;
-                        goto finish;
-                    }
-                    A.seg_cell[idx] = S.cur;
-                    if (PREC == HG_FP64)
-                        static_cast<double *>(A.seg_ds)[idx] = ds;
-                    else
-                        static_cast<float *>(A.seg_ds)[idx] = __double2float_rn(ds);
-                } else {
-                    const double v = wk * ds;
-                    if (PREC == 0)
-                        atomicAdd(static_cast<double *>(A.grad) + S.cur, v);
-                    else
-                        atomicAdd(static_cast<float *>(A.grad) + S.cur, __double2float_rn(v));
-                }
-                nc++;
-            }
-            if (r1 == WALK_END) goto finish;
-            if (ray_advance<KIND>(G, smem, A.n_smem, S, L, ax, tex, &st) == WALK_END) goto finish;
-            continue;
-        }
-    finish:
-        if (MODE == MODE_TAU) {
-            if (PREC == HG_FP64)
-                static_cast<double *>(A.tau)[ray] = A.kappa * acc;
-            else
-                static_cast<float *>(A.tau)[ray] = acc32;
-            A.ncross[ray] = nc;
-            if (A.status) A.status[ray] = (uint8_t)st;
-        } else if (MODE == MODE_FILL) {
-            if (A.status && st) A.status[ray] |= (uint8_t)st;
-        } else {
-            if (A.status) A.status[ray] = (uint8_t)st;
-        }
-        ray = -1;
-    }
+    stage_nodes(A.G.nodes, A.n_smem * node_bytes, smem);
+    GridRays src;
+    src.G = &A.G;
+    src.n = A.n;
+    src.cursor = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    src.stride = (int64_t)gridDim.x * blockDim.x;
+    src.counter = A.counter;
+    src.max_steps = (int32_t)(A.max_steps < 0x7fffffff ? A.max_steps : 0x7fffffff);
+    src.dyn = A.dyn != 0;
+    WalkIO io;
+    io.o = A.o;
+    io.d = A.d;
+    io.smax = A.smax;
+    io.starts = A.starts;
+    io.kappa = A.kappa;
+    io.tau = A.tau;
+    io.ncross = A.ncross;
+    io.status = A.status;
+    io.seg_off = A.seg_off;
+    io.seg_cell = A.seg_cell;
+    io.seg_ds = A.seg_ds;
+    io.seg_cap = A.seg_cap;
+    io.w = A.w;
+    io.grad = A.grad;
+    io.rho_ext = A.rho_ext;
+    walk_loop<KIND, MODE, PREC>(src, io, smem, A.n_smem);
 }
 
 // ------------------------------------------------------------------ launch plumbing

@@ -259,12 +259,12 @@ __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned c
     return R;
 }
 
-// Take a ray for walking from its start record.  Returns WALK_GO with S and
-// L filled, or WALK_END with the setup status in *st.
-__device__ __forceinline__ int ray_resume(const DevGrid &G, const double *__restrict__ o,
-                                          const double *__restrict__ d, const double *__restrict__ smax,
-                                          const RayStart *__restrict__ starts, int64_t r, RayState &S, Leaf &L,
-                                          uint32_t *st) {
+// Take a ray for walking from its start record.  Returns WALK_GO with S
+// filled (S.cur = first leaf, not loaded yet), or WALK_END with the setup
+// status in *st.
+__device__ __forceinline__ int ray_resume(const double *__restrict__ o, const double *__restrict__ d,
+                                          const double *__restrict__ smax, const RayStart *__restrict__ starts,
+                                          int64_t r, RayState &S, uint32_t *st) {
     const double2 *q = reinterpret_cast<const double2 *>(starts + r);
     const double2 a = __ldg(q), b = __ldg(q + 1);
     const int4 c = __ldg(reinterpret_cast<const int4 *>(q + 2));
@@ -277,7 +277,7 @@ __device__ __forceinline__ int ray_resume(const DevGrid &G, const double *__rest
     S.ktcur = __double_as_longlong(b.y);
     S.cur = c.x;
     S.sg = (uint32_t)c.y & 0xffu;
-    double o0 = o[3 * r], o1 = o[3 * r + 1], o2 = o[3 * r + 2];
+    const double o0 = o[3 * r], o1 = o[3 * r + 1], o2 = o[3 * r + 2];
     S.o0 = (o0 == 0.0) ? 0.0 : o0;
     S.o1 = (o1 == 0.0) ? 0.0 : o1;
     S.o2 = (o2 == 0.0) ? 0.0 : o2;
@@ -286,7 +286,6 @@ __device__ __forceinline__ int ray_resume(const DevGrid &G, const double *__rest
     S.k2 = d[3 * r + 2];
     S.ktend = smax ? okey(smax[r]) : KEY_INF;
     S.steps = 0;
-    load_leaf(G.rec, S.cur, L);
     return WALK_GO;
 }
 
@@ -332,75 +331,239 @@ __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Le
     return WALK_GO;
 }
 
-// Move to the leaf beyond the exit wall: the wall's neighbor list (head
-// stored in the leaf), then a top-down search for edge and corner exits
-// and long lists.  Returns WALK_GO, or WALK_END when the exit point lies on
-// the domain surface with the direction pointing out (or the ray is lost).
-template <int KIND>
-__device__ __forceinline__ int ray_advance(const DevGrid &G, const unsigned char *snodes, int n_smem, RayState &S,
-                                           Leaf &L, int ax, double tex, uint32_t *st) {
+// The next record to load and how to treat it.
+enum { CAND_ENTER = 0, CAND_TEST = 1 };
+struct Cand {
+    int32_t id;     // record to load next
+    int32_t mode;   // CAND_ENTER: known to contain the exit point; CAND_TEST: a listed neighbor
+    int32_t ax;     // exit axis
+    int32_t e;      // next tail entry to try
+    int32_t ntail;  // tail entries of the exit wall's list (-1: not read yet)
+    uint32_t off;   // where they start
+    int32_t prev;   // the leaf being left
+    long long p1, p2;  // keys of the exit point on the two other axes (b1 < b2)
+};
+
+// After an exit through axis ax at time tex: the exit point (the wall on
+// the exit axis, o + d t clamped to the leaf on the others) and the first
+// neighbor to test, the head of the exit wall's list stored in the leaf.
+__device__ __forceinline__ void cand_first(const RayState &S, const Leaf &L, int ax, double tex, Cand &C) {
     const uint32_t sg = S.sg;
-    const bool pax = dpos(sg, ax);
-    const int w = 2 * ax + (pax ? 1 : 0);
-    const int32_t nxt = L.first(w);
-    // exit point: the wall on the exit axis, o + d t clamped to the leaf on the others
+    const int w = 2 * ax + (dpos(sg, ax) ? 1 : 0);
     const int b1 = (ax == 0) ? 1 : 0;
     const int b2 = (ax == 2) ? 1 : 2;
-    const long long wall = pax ? L.hi(ax) : L.lo(ax);
-    long long p1, p2;
-    {
-        const double ob1 = sel3(b1, S.o0, S.o1, S.o2), kb1 = sel3(b1, S.k0, S.k1, S.k2);
-        const double ob2 = sel3(b2, S.o0, S.o1, S.o2), kb2 = sel3(b2, S.k0, S.k1, S.k2);
-        p1 = okey(ob1 + kb1 * tex);
-        p2 = okey(ob2 + kb2 * tex);
-        const long long l1 = L.lo(b1), h1 = L.hi(b1), l2 = L.lo(b2), h2 = L.hi(b2);
-        if (p1 < l1) p1 = l1;
-        if (p1 > h1) p1 = h1;
-        if (p2 < l2) p2 = l2;
-        if (p2 > h2) p2 = h2;
-    }
-    const bool pos1 = dpos(sg, b1), neg1 = dneg(sg, b1), pos2 = dpos(sg, b2), neg2 = dneg(sg, b2);
-    // an exit point on the domain surface with the direction pointing out ends the path
-    if (!in_axis(p1, G.klo[b1], G.khi[b1], pos1, neg1, true) || !in_axis(p2, G.klo[b2], G.khi[b2], pos2, neg2, true))
-        return WALK_END;
-    // neighbor-list search.  What is still needed from the current leaf is
-    // taken out first; each candidate is then loaded straight into L.
-    const int cw = L.cnt(w);
-    uint32_t off = L.base;
-    for (int v = 0; v < w; v++) {
-        const int c = L.cnt(v);
-        if (c >= 2 && c <= G.scan_limit) off += (uint32_t)(c - 1);
-    }
-    const uint32_t ub1 = 1u << b1, ub2 = 1u << b2;
-    load_leaf(G.rec, nxt, L);  // the list head is stored in the leaf itself
-    if (in_axis(p1, L.lo(b1), L.hi(b1), pos1, neg1, L.flags() & ub1) &&
-        in_axis(p2, L.lo(b2), L.hi(b2), pos2, neg2, L.flags() & ub2)) {
-        S.cur = nxt;
-        return WALK_GO;
-    }
-    if (cw >= 2 && cw <= G.scan_limit) {
-        for (int e = 0; e < cw - 1; e++) {
-            const int32_t j = __ldg(G.tail + off + e);
-            load_leaf(G.rec, j, L);
-            if (in_axis(p1, L.lo(b1), L.hi(b1), pos1, neg1, L.flags() & ub1) &&
-                in_axis(p2, L.lo(b2), L.hi(b2), pos2, neg2, L.flags() & ub2)) {
-                S.cur = j;
-                return WALK_GO;
-            }
+    const double ob1 = sel3(b1, S.o0, S.o1, S.o2), kb1 = sel3(b1, S.k0, S.k1, S.k2);
+    const double ob2 = sel3(b2, S.o0, S.o1, S.o2), kb2 = sel3(b2, S.k0, S.k1, S.k2);
+    long long p1 = okey(ob1 + kb1 * tex);
+    long long p2 = okey(ob2 + kb2 * tex);
+    const long long l1 = L.lo(b1), h1 = L.hi(b1), l2 = L.lo(b2), h2 = L.hi(b2);
+    if (p1 < l1) p1 = l1;
+    if (p1 > h1) p1 = h1;
+    if (p2 < l2) p2 = l2;
+    if (p2 > h2) p2 = h2;
+    C.id = L.first(w);
+    C.mode = CAND_TEST;
+    C.ax = ax;
+    C.e = 0;
+    C.ntail = -1;
+    C.prev = S.cur;
+    C.p1 = p1;
+    C.p2 = p2;
+}
+
+// Does the freshly loaded listed neighbor L contain the exit point?  (The
+// direction-aware rule on the two other axes; on the exit axis every listed
+// neighbor starts at the wall.)
+__device__ __forceinline__ bool cand_contains(uint32_t sg, const Leaf &L, const Cand &C) {
+    const int b1 = (C.ax == 0) ? 1 : 0;
+    const int b2 = (C.ax == 2) ? 1 : 2;
+    return in_axis(C.p1, L.lo(b1), L.hi(b1), dpos(sg, b1), dneg(sg, b1), (L.flags() >> b1) & 1u) &&
+           in_axis(C.p2, L.lo(b2), L.hi(b2), dpos(sg, b2), dneg(sg, b2), (L.flags() >> b2) & 1u);
+}
+
+// Where the rest of the exit wall's list is: read from the leaf being left
+// (only needed when the head does not contain the exit point).
+__device__ __forceinline__ void cand_tail_info(const DevGrid &G, uint32_t sg, Cand &C) {
+    const int w = 2 * C.ax + (dpos(sg, C.ax) ? 1 : 0);
+    const unsigned char *rec = reinterpret_cast<const unsigned char *>(G.rec + C.prev);
+    const double2 d = __ldg(reinterpret_cast<const double2 *>(rec + 48));
+    const int4 f = __ldg(reinterpret_cast<const int4 *>(rec + 80));
+    const uint32_t c03 = (uint32_t)f.z, c45 = (uint32_t)f.w;
+    uint32_t off = (uint32_t)((unsigned long long)__double_as_longlong(d.y) >> 32);
+    int cw = 0;
+    for (int v = 0; v <= w; v++) {
+        const int c = v < 4 ? (int)((c03 >> (8 * v)) & 255u) : (int)((c45 >> (8 * (v - 4))) & 255u);
+        if (v == w) {
+            cw = c;
+        } else if (c >= 2 && c <= G.scan_limit) {
+            off += (uint32_t)(c - 1);
         }
     }
-    // edge or corner exit, or a long list: locate the exit point top-down
-    const long long q0 = (ax == 0) ? wall : (b1 == 0 ? p1 : p2);
-    const long long q1 = (ax == 1) ? wall : (b1 == 1 ? p1 : p2);
-    const long long q2 = (ax == 2) ? wall : p2;
-    const int32_t j = descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg);
-    if (j < 0) {
-        *st = HG_RAY_LOST;
-        return WALK_END;
+    C.off = off;
+    C.ntail = (cw >= 2 && cw <= G.scan_limit) ? cw - 1 : 0;
+}
+
+// No listed neighbor contains the exit point: an exit point on the domain
+// surface with the direction pointing out ends the path (returns true);
+// otherwise the caller locates the point top-down.
+__device__ __forceinline__ bool cand_leaves_domain(const DevGrid &G, uint32_t sg, const Cand &C) {
+    const int b1 = (C.ax == 0) ? 1 : 0;
+    const int b2 = (C.ax == 2) ? 1 : 2;
+    return !in_axis(C.p1, G.klo[b1], G.khi[b1], dpos(sg, b1), dneg(sg, b1), true) ||
+           !in_axis(C.p2, G.klo[b2], G.khi[b2], dpos(sg, b2), dneg(sg, b2), true);
+}
+
+// Top-down location of the exit point: the wall on the exit axis (the near
+// bound of the listed neighbor L) and the clamped point on the others.
+template <int KIND>
+__device__ __forceinline__ int32_t cand_descend(const DevGrid &G, const unsigned char *snodes, int n_smem,
+                                                uint32_t sg, const Leaf &L, const Cand &C) {
+    const int ax = C.ax;
+    const long long wall = dpos(sg, ax) ? L.lo(ax) : L.hi(ax);
+    const int b1 = (ax == 0) ? 1 : 0;
+    const long long q0 = (ax == 0) ? wall : (b1 == 0 ? C.p1 : C.p2);
+    const long long q1 = (ax == 1) ? wall : (b1 == 1 ? C.p1 : C.p2);
+    const long long q2 = (ax == 2) ? wall : C.p2;
+    return descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg);
+}
+
+// Outputs and inputs of one walking launch.
+enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2 };
+struct WalkIO {
+    const double *o;
+    const double *d;
+    const double *smax;
+    const RayStart *starts;
+    double kappa;
+    void *tau;
+    int32_t *ncross;
+    uint8_t *status;
+    const int64_t *seg_off;
+    int32_t *seg_cell;
+    void *seg_ds;
+    int64_t seg_cap;
+    const float *w;
+    void *grad;
+    const double *rho_ext;  // densities replacing the grid's own (MODE_TAU), or NULL
+};
+
+// The walking loop of one thread.  Each iteration loads exactly one leaf
+// record -- the first leaf of a new ray, a listed neighbor to test (the
+// head, or the next tail entry after a miss), or the leaf a top-down
+// search found -- so a lane that missed the list head costs its warp one
+// more iteration instead of a chain of dependent loads inside one.
+// Src hands out rays: bool next(int64_t &ray, const DevGrid *&G, int32_t &max_steps).
+//   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
+//   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
+template <int KIND, int MODE, int PREC, class Src>
+__device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem) {
+    const DevGrid *Gp = nullptr;
+    int64_t ray = 0;
+    int32_t max_steps = 0;
+    RayState S;
+    Leaf L;
+    Cand C;
+    double acc = 0.0;     // FP64 sum of rho*ds
+    float acc32 = 0.0f;   // FP32 Kahan sum
+    float comp32 = 0.0f;  // Kahan compensation
+    int32_t nc = 0;
+    int64_t seg_base = 0;
+    double wk = 0.0;  // kappa * w for the adjoint
+    uint32_t st = 0;
+    bool have = false;
+    const float kappa32 = (float)io.kappa;
+    for (;;) {
+        if (!have) {
+            if (!src.next(ray, Gp, max_steps)) break;
+            acc = 0.0;
+            acc32 = 0.0f;
+            comp32 = 0.0f;
+            nc = 0;
+            if (MODE == MODE_FILL) seg_base = io.seg_off[ray];
+            if (MODE == MODE_ADJ) wk = io.kappa * (double)io.w[ray];
+            have = true;
+            if (ray_resume(io.o, io.d, io.smax, io.starts, ray, S, &st) == WALK_END) goto finish;
+            C.id = S.cur;
+            C.mode = CAND_ENTER;
+        }
+        {
+            const DevGrid &G = *Gp;
+            load_leaf(G.rec, C.id, L);
+            if (C.mode == CAND_TEST && !cand_contains(S.sg, L, C)) {
+                if (C.ntail < 0) cand_tail_info(G, S.sg, C);
+                if (C.e < C.ntail) {
+                    C.id = __ldg(G.tail + C.off + C.e);
+                    C.e++;
+                    continue;
+                }
+                if (cand_leaves_domain(G, S.sg, C)) goto finish;
+                // edge or corner exit, or a long list: locate the exit point top-down
+                const int32_t j = cand_descend<KIND>(G, snodes, n_smem, S.sg, L, C);
+                if (j < 0) {
+                    st = HG_RAY_LOST;
+                    goto finish;
+                }
+                C.id = j;
+                C.mode = CAND_ENTER;
+                continue;
+            }
+            S.cur = C.id;
+            double ds, tex;
+            int ax;
+            const int r = ray_exit(max_steps, S, L, &ds, &ax, &tex, &st);
+            if (ds != 0.0) {
+                if (MODE == MODE_TAU) {
+                    if (PREC == HG_FP64) {
+                        const double rho = io.rho_ext ? __ldg(io.rho_ext + S.cur) : L.rho;
+                        acc = acc + rho * ds;
+                    } else {
+                        const float rho32 = io.rho_ext ? __double2float_rn(__ldg(io.rho_ext + S.cur)) : L.rho32;
+                        const float kr32 = __fmul_rn(kappa32, rho32);
+                        const float y = __fsub_rn(__fmul_rn(kr32, __double2float_rn(ds)), comp32);
+                        const float t = __fadd_rn(acc32, y);
+                        comp32 = __fsub_rn(__fsub_rn(t, acc32), y);
+                        acc32 = t;
+                    }
+                } else if (MODE == MODE_FILL) {
+                    const int64_t idx = seg_base + nc;
+                    if (idx >= io.seg_cap) {
+                        st |= HG_RAY_OVERFLOW;
+                        goto finish;
+                    }
+                    io.seg_cell[idx] = S.cur;
+                    if (PREC == HG_FP64)
+                        static_cast<double *>(io.seg_ds)[idx] = ds;
+                    else
+                        static_cast<float *>(io.seg_ds)[idx] = __double2float_rn(ds);
+                } else {
+                    const double v = wk * ds;
+                    if (PREC == 0)
+                        atomicAdd(static_cast<double *>(io.grad) + S.cur, v);
+                    else
+                        atomicAdd(static_cast<float *>(io.grad) + S.cur, __double2float_rn(v));
+                }
+                nc++;
+            }
+            if (r == WALK_GO) {
+                cand_first(S, L, ax, tex, C);
+                continue;
+            }
+        }
+    finish:
+        if (MODE == MODE_TAU) {
+            if (PREC == HG_FP64)
+                static_cast<double *>(io.tau)[ray] = io.kappa * acc;
+            else
+                static_cast<float *>(io.tau)[ray] = acc32;
+            io.ncross[ray] = nc;
+            if (io.status) io.status[ray] = (uint8_t)st;
+        } else if (MODE == MODE_FILL) {
+            if (io.status && st) io.status[ray] |= (uint8_t)st;
+        } else {
+            if (io.status) io.status[ray] = (uint8_t)st;
+        }
+        have = false;
     }
-    S.cur = j;
-    load_leaf(G.rec, j, L);
-    return WALK_GO;
 }
 
 }  // namespace hg
