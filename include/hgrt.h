@@ -190,7 +190,10 @@ typedef struct hg_trace_opts {
     int32_t precision;   /* HG_FP64 or HG_FP32K */
     int32_t block;       /* threads per block (32..256, multiple of 32); 0 = tuned or default */
     int32_t smem_nodes;  /* top tree nodes staged in shared memory (clamped to 200 KB); -1 = tuned or default */
-    int32_t schedule;    /* 0 = tuned or default, 1 = static ray stride, 2 = dynamic (warp-aggregated counter) */
+    int32_t schedule;    /* 0 = tuned or automatic; 1 = static ray stride; 2 = dynamic queue (warp-aggregated
+                            counter) in input order; 3 = dynamic queue, rays with the most estimated
+                            crossings first (automatic when there are fewer than 48 rays per
+                            resident thread) */
     int32_t min_blocks;  /* 0 = tuned or default (3); 3 or 4 resident 256-thread blocks per SM the
                             kernel's register budget is cut for */
     int32_t reserved;

@@ -273,7 +273,7 @@ extern "C" hg_status hg_autotune(hg_grid *g, int64_t n, const double *o, const d
     hg_trace_opts win{};
     float win_ms = 1e30f;
     hg_status st = HG_OK;
-    for (int sched = 1; sched <= 2 && st == HG_OK; sched++)
+    for (int sched = 1; sched <= 3 && st == HG_OK; sched++)
         for (int occ = 3; occ <= 4; occ++)
             for (int bl : blocks)
                 for (int kb : smem_kb) {

@@ -258,6 +258,40 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
             }
         }
         if (tail.empty()) tail.push_back(-1);
+        // expected crossings per unit length on a coarse lattice (work estimate)
+        std::vector<float> work((size_t)hg::kWorkN * hg::kWorkN * hg::kWorkN, 0.0f);
+        {
+            const int N = hg::kWorkN;
+            double ext[3], cvol = 1.0;
+            for (int a = 0; a < 3; a++) {
+                ext[a] = D.node_hi[a] - D.node_lo[a];
+                cvol *= ext[a] / N;
+            }
+            std::vector<double> acc(work.size(), 0.0);
+            for (int64_t i = 0; i < nl; i++) {
+                const double *lo = D.node_lo + 3 * leaf_node[i], *hi = D.node_hi + 3 * leaf_node[i];
+                const double a = hi[0] - lo[0], b = hi[1] - lo[1], c = hi[2] - lo[2];
+                const double rate = (a * b + b * c + c * a) / (2.0 * a * b * c);
+                int c0[3], c1[3];
+                for (int ax = 0; ax < 3; ax++) {
+                    c0[ax] = std::max(0, std::min(N - 1, (int)std::floor((lo[ax] - D.node_lo[ax]) / ext[ax] * N)));
+                    c1[ax] = std::max(0, std::min(N - 1, (int)std::ceil((hi[ax] - D.node_lo[ax]) / ext[ax] * N) - 1));
+                }
+                for (int z = c0[2]; z <= c1[2]; z++)
+                    for (int y = c0[1]; y <= c1[1]; y++)
+                        for (int x = c0[0]; x <= c1[0]; x++) {
+                            const int cc[3] = {x, y, z};
+                            double ov = 1.0;
+                            for (int ax = 0; ax < 3; ax++) {
+                                const double l = D.node_lo[ax] + ext[ax] * cc[ax] / N;
+                                const double h = D.node_lo[ax] + ext[ax] * (cc[ax] + 1) / N;
+                                ov *= std::max(0.0, std::min(h, hi[ax]) - std::max(l, lo[ax]));
+                            }
+                            acc[(size_t)x + N * ((size_t)y + N * z)] += ov * rate;
+                        }
+            }
+            for (size_t j = 0; j < work.size(); j++) work[j] = (float)(acc[j] / cvol);
+        }
 
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -270,7 +304,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
         };
         if ((e = upload(&g->d_rec, rec.data(), rec.size() * sizeof(hg::LeafRec))) != cudaSuccess ||
             (e = upload(&g->d_tail, tail.data(), tail.size() * sizeof(int32_t))) != cudaSuccess ||
-            (e = upload(&g->d_nodes, nodes.data(), nodes.size())) != cudaSuccess) {
+            (e = upload(&g->d_nodes, nodes.data(), nodes.size())) != cudaSuccess ||
+            (e = upload(&g->d_work, work.data(), work.size() * sizeof(float))) != cudaSuccess) {
             hg_status st = cuda_fail(e, "hg_load_grid: upload");
             hg_free_grid(g.release());
             return st;
@@ -279,6 +314,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
         G.rec = static_cast<const hg::LeafRec *>(g->d_rec);
         G.tail = static_cast<const int32_t *>(g->d_tail);
         G.nodes = g->d_nodes;
+        G.work = static_cast<const float *>(g->d_work);
+        G.work_n = hg::kWorkN;
         for (int a = 0; a < 3; a++) {
             G.dlo[a] = D.node_lo[a];
             G.dhi[a] = D.node_hi[a];
@@ -296,7 +333,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
         I.n_nodes = n;
         I.n_leaves = nl;
         I.n_tail = (int64_t)tail.size();
-        I.device_bytes = (int64_t)(rec.size() * sizeof(hg::LeafRec) + tail.size() * 4 + nodes.size());
+        I.device_bytes = (int64_t)(rec.size() * sizeof(hg::LeafRec) + tail.size() * 4 + nodes.size() +
+                                   work.size() * sizeof(float));
         I.long_walls = long_walls;
         for (int a = 0; a < 3; a++) {
             I.lo[a] = G.dlo[a];
@@ -318,6 +356,7 @@ extern "C" void hg_free_grid(hg_grid *g) {
     if (g->d_rec) cudaFree(g->d_rec);
     if (g->d_tail) cudaFree(g->d_tail);
     if (g->d_nodes) cudaFree(g->d_nodes);
+    if (g->d_work) cudaFree(g->d_work);
     if (cur != g->device) cudaSetDevice(cur);
     delete g;
 }

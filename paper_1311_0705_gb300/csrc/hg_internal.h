@@ -70,6 +70,7 @@ struct DevGrid {
     const LeafRec *rec;
     const int32_t *tail;
     const void *nodes;
+    const float *work;         // [work_n^3] expected crossings per unit length on a coarse lattice
     double dlo[3], dhi[3];
     long long klo[3], khi[3];  // keys of the domain bounds
     int64_t n_leaves;
@@ -77,8 +78,13 @@ struct DevGrid {
     int32_t kind;
     int32_t max_depth;
     int32_t scan_limit;
-    int32_t pad;
+    int32_t work_n;
 };
+
+// Coarse lattice of the expected number of leaf crossings per unit path
+// length (volume average of S/(4V) over the leaves, Cauchy's mean chord),
+// used only to order rays by their estimated work.
+constexpr int kWorkN = 16;
 
 struct TuneEntry {
     int valid = 0;
@@ -96,6 +102,7 @@ struct hg_grid {
     void *d_rec = nullptr;
     void *d_tail = nullptr;
     void *d_nodes = nullptr;
+    void *d_work = nullptr;
     int device = 0;
     hg::TuneEntry tuned[2];
 };

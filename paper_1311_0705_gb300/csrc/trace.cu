@@ -34,6 +34,7 @@ struct TraceArgs {
     int64_t max_steps;
     unsigned long long *counter;
     const RayStart *starts;
+    const int64_t *order;  // queue position -> ray (most work first), or NULL
     int n_smem;
     int dyn;
 };
@@ -49,14 +50,67 @@ __device__ __forceinline__ void stage_nodes(const void *nodes, int bytes, unsign
 // Setup pass: one ray per thread, every thread doing the same work (checks,
 // 1/d, clip, top-down location of the first leaf), so that the walking
 // kernel's refill is a handful of loads instead of a divergent descent.
+//
+// Crossings per path are heavy-tailed (on the disk grids the median path
+// crosses 5 leaves, the longest several hundred), and a launch lasts at
+// least as long as its longest path.  So with a non-NULL bucket_count the
+// pass also sorts the rays into kBuckets classes of estimated work (the
+// coarse-lattice estimate, or the exact count when seg_off gives it) and
+// the dynamic queue hands out the heaviest paths first.
+constexpr int kBuckets = 32;
+
+__device__ __forceinline__ int work_bucket(float w) {
+    const int b = (int)(__log2f(1.0f + fmaxf(w, 0.0f)) * 3.0f);
+    return kBuckets - 1 - (b < 0 ? 0 : (b > kBuckets - 1 ? kBuckets - 1 : b));  // 0 = most work
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) setup_kernel(const DevGrid G, int64_t n, const double *__restrict__ o,
                                                     const double *__restrict__ d, const double *__restrict__ smax,
-                                                    RayStart *starts, int n_smem) {
+                                                    RayStart *starts, int n_smem, unsigned long long *bucket_count,
+                                                    const int64_t *__restrict__ seg_off) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned int hist[kBuckets];
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
     stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        starts[r] = ray_setup<KIND>(G, smem, n_smem, o, d, smax, r);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        RayStart R = ray_setup<KIND>(G, smem, n_smem, o, d, smax, r, bucket_count != nullptr && !seg_off);
+        if (seg_off) R.work = (float)(seg_off[r + 1] - seg_off[r]);
+        starts[r] = R;
+        if (bucket_count) atomicAdd(&hist[work_bucket(R.work)], 1u);
+    }
+    if (bucket_count) {
+        __syncthreads();
+        if (threadIdx.x < kBuckets && hist[threadIdx.x]) atomicAdd(&bucket_count[threadIdx.x], hist[threadIdx.x]);
+    }
+}
+
+// Queue order from the bucket counts: ray r goes to the next free slot of
+// its bucket (lanes of a warp with the same bucket share one atomic; the
+// order inside a bucket is arbitrary and results do not depend on it).
+__global__ void __launch_bounds__(256) order_kernel(int64_t n, const RayStart *__restrict__ starts,
+                                                    const unsigned long long *bucket_count,
+                                                    unsigned long long *bucket_fill, int64_t *order) {
+    __shared__ unsigned long long base[kBuckets];
+    if (threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int b = 0; b < kBuckets; b++) {
+            base[b] = acc;
+            acc += bucket_count[b];
+        }
+    }
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31u;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int b = work_bucket(starts[r].work);
+        const unsigned mask = __match_any_sync(__activemask(), b);
+        const int leader = __ffs(mask) - 1;
+        const unsigned rank = __popc(mask & ((1u << lane) - 1u));
+        unsigned long long slot = 0;
+        if ((int)lane == leader) slot = atomicAdd(&bucket_fill[b], (unsigned long long)__popc(mask));
+        slot = __shfl_sync(mask, slot, leader);
+        order[base[b] + slot + rank] = r;
+    }
 }
 
 // Rays of one grid for the walking loop: a static stride, or a
@@ -67,6 +121,7 @@ struct GridRays {
     int64_t cursor;
     int64_t stride;
     unsigned long long *counter;
+    const int64_t *order;
     int32_t max_steps;
     bool dyn;
     __device__ __forceinline__ bool next(int64_t &ray, const DevGrid *&g, int32_t &ms) {
@@ -78,10 +133,11 @@ struct GridRays {
             if (grp.thread_rank() == 0) base = atomicAdd(counter, (unsigned long long)grp.size());
             base = grp.shfl(base, 0);
             ray = (int64_t)(base + grp.thread_rank());
-        } else {
-            ray = cursor;
-            cursor += stride;
+            if (ray < n && order) ray = order[ray];
+            return ray < n;
         }
+        ray = cursor;
+        cursor += stride;
         return ray < n;
     }
 };
@@ -102,6 +158,7 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     src.cursor = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     src.stride = (int64_t)gridDim.x * blockDim.x;
     src.counter = A.counter;
+    src.order = A.order;
     src.max_steps = (int32_t)(A.max_steps < 0x7fffffff ? A.max_steps : 0x7fffffff);
     src.dyn = A.dyn != 0;
     WalkIO io;
@@ -165,7 +222,7 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
     block = (opts && opts->block > 0) ? opts->block : (T.valid ? T.block : 256);
     smem_nodes = (opts && opts->smem_nodes >= 0) ? opts->smem_nodes
                                                   : (T.valid ? T.smem_nodes : (g->d.kind == HG_KDTREE ? 2048 : 1024));
-    schedule = (opts && opts->schedule > 0) ? opts->schedule : (T.valid ? T.schedule : 2);
+    schedule = (opts && opts->schedule > 0) ? opts->schedule : (T.valid ? T.schedule : 0);
     min_blocks = (opts && opts->min_blocks > 0) ? opts->min_blocks : (T.valid ? T.min_blocks : 3);
     max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 4 * g->d.n_leaves + 64;
     if (block < 32 || block > 256 || block % 32) {
@@ -176,8 +233,8 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
         set_error("min_blocks must be 3 or 4");
         return HG_EINVAL;
     }
-    if (schedule != 1 && schedule != 2) {
-        set_error("schedule must be 1 or 2");
+    if (schedule < 0 || schedule > 3) {
+        set_error("schedule must be 0 (auto), 1, 2 or 3");
         return HG_EINVAL;
     }
     // clamp to the node count and to 200 KB of shared memory
@@ -213,34 +270,61 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
     int64_t blocks = (int64_t)per_sm * sm_count();
     const int64_t need = (A.n + block - 1) / block;
     if (blocks > need) blocks = need;
+    // auto schedule: order by estimated work only when each resident thread
+    // gets few paths (then the heaviest paths would otherwise set the end)
+    if (schedule == 0) schedule = (A.n < 48 * blocks * block) ? 3 : 2;
     A.n_smem = smem_nodes;
-    A.dyn = (schedule == 2);
+    A.dyn = (schedule >= 2);
+    const bool ordered = (schedule == 3);
     // setup pass into a scratch array of start records
-    RayStart *starts = nullptr;
-    e = cudaMallocAsync((void **)&starts, (size_t)A.n * sizeof(RayStart), stream);
+    // scratch: start records, and for the dynamic schedule the work-ordered
+    // queue with its bucket counters
+    const size_t start_bytes = ((size_t)A.n * sizeof(RayStart) + 255) / 256 * 256;
+    const size_t order_bytes = ordered ? ((size_t)A.n * sizeof(int64_t) + 255) / 256 * 256 : 0;
+    const size_t count_bytes = ordered ? 2 * kBuckets * sizeof(unsigned long long) : 0;
+    unsigned char *scratch = nullptr;
+    e = cudaMallocAsync((void **)&scratch, start_bytes + order_bytes + count_bytes, stream);
     if (e != cudaSuccess) return cuda_err(e, "ray start scratch");
+    RayStart *starts = reinterpret_cast<RayStart *>(scratch);
+    int64_t *order = ordered ? reinterpret_cast<int64_t *>(scratch + start_bytes) : nullptr;
+    unsigned long long *counts =
+        ordered ? reinterpret_cast<unsigned long long *>(scratch + start_bytes + order_bytes) : nullptr;
+    if (counts) {
+        e = cudaMemsetAsync(counts, 0, count_bytes, stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(scratch, stream);
+            return cuda_err(e, "scratch reset");
+        }
+    }
     {
+        // the fill pass knows each ray's exact crossing count from its offsets
+        const int64_t *exact = (mode == MODE_FILL) ? A.seg_off : nullptr;
         const int64_t sblocks = std::min<int64_t>((A.n + 255) / 256, (int64_t)sm_count() * 8);
         if (g->d.kind == HG_KDTREE)
             setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, A.n, A.o, A.d, A.smax, starts,
-                                                                             smem_nodes);
+                                                                             smem_nodes, counts, exact);
         else
             setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, A.n, A.o, A.d, A.smax, starts,
-                                                                             smem_nodes);
+                                                                             smem_nodes, counts, exact);
         note_launches(1);
+        if (order) {
+            order_kernel<<<(unsigned)sblocks, 256, 0, stream>>>(A.n, starts, counts, counts + kBuckets, order);
+            note_launches(1);
+        }
     }
     A.starts = starts;
+    A.order = order;
     unsigned long long *ctr = nullptr;
     if (A.dyn) {
         e = cudaMallocAsync((void **)&ctr, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) {
-            cudaFreeAsync(starts, stream);
+            cudaFreeAsync(scratch, stream);
             return cuda_err(e, "scratch counter");
         }
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) {
             cudaFreeAsync(ctr, stream);
-            cudaFreeAsync(starts, stream);
+            cudaFreeAsync(scratch, stream);
             return cuda_err(e, "scratch counter");
         }
         A.counter = ctr;
@@ -249,7 +333,7 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
     e = cudaGetLastError();
     note_launches(1);
     if (ctr) cudaFreeAsync(ctr, stream);
-    cudaFreeAsync(starts, stream);
+    cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_err(e, "trace launch");
     return HG_OK;
 }
@@ -635,9 +719,11 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
     }
     const int64_t sblocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     if (g->d.kind == HG_KDTREE)
-        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes);
+        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes,
+                                                                         nullptr, nullptr);
     else
-        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes);
+        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes,
+                                                                         nullptr, nullptr);
     k<<<(unsigned)blocks, block, smem, stream>>>(A);
     note_launches(2);
     e = cudaGetLastError();

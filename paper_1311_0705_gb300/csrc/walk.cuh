@@ -170,11 +170,55 @@ struct alignas(16) RayStart {
     long long ktstart;     // key of the entry time
     int32_t cur;           // first leaf, or -1 when the ray does not walk
     uint32_t sg;           // direction sign bits | status bits << 8
-    int64_t pad;
+    float work;            // estimated number of crossings (orders the queue)
+    int32_t pad;
 };
 static_assert(sizeof(RayStart) == 48 && offsetof(RayStart, ktstart) == 24 && offsetof(RayStart, cur) == 32 &&
                   offsetof(RayStart, sg) == 36,
               "ray_resume reads the start record as two double2 and one int4");
+
+// Estimated number of leaf crossings of the path o + t d, t in [t0, t1]: a
+// single-precision march through the coarse lattice of expected crossings
+// per unit length.  Only orders the work; it never affects a result.
+__device__ __forceinline__ float estimate_work(const DevGrid &G, const double *o, const double *d, double t0,
+                                               double t1) {
+    const int N = G.work_n;
+    if (!G.work || N <= 0 || !(t1 > t0)) return 0.0f;
+    float sc[3], p[3], k[3];
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        sc[a] = (float)N / (float)(G.dhi[a] - G.dlo[a]);
+        k[a] = (float)d[a] * sc[a];  // lattice units per unit t
+        p[a] = (float)((o[a] + d[a] * t0) - G.dlo[a]) * sc[a];
+        int ci = (int)floorf(p[a]);
+        c[a] = ci < 0 ? 0 : (ci > N - 1 ? N - 1 : ci);
+    }
+    float t = (float)t0;
+    const float tend = (float)t1;
+    float e = 0.0f;
+    for (int it = 0; it < 3 * N + 3 && t < tend; it++) {
+        float tn = tend;
+        int ax = -1;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (k[a] == 0.0f) continue;
+            const float wall = (float)(k[a] > 0.0f ? c[a] + 1 : c[a]);
+            const float ta = t + (wall - (p[a] + k[a] * (t - (float)t0))) / k[a];
+            if (ta < tn) {
+                tn = ta;
+                ax = a;
+            }
+        }
+        if (tn < t) tn = t;
+        e += __ldg(G.work + c[0] + N * (c[1] + N * c[2])) * (tn - t);
+        t = tn;
+        if (ax < 0) break;
+        c[ax] += k[ax] > 0.0f ? 1 : -1;
+        if (c[ax] < 0 || c[ax] >= N) break;
+    }
+    return e;
+}
 
 // Set up a ray (the first-cell location of Sect. 2.3): checks, 1/d, clip
 // against the domain, top-down descent to the first leaf.  Runs once per
@@ -182,12 +226,13 @@ static_assert(sizeof(RayStart) == 48 && offsetof(RayStart, ktstart) == 24 && off
 template <int KIND>
 __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned char *snodes, int n_smem,
                                               const double *__restrict__ o, const double *__restrict__ d,
-                                              const double *__restrict__ smax, int64_t r) {
+                                              const double *__restrict__ smax, int64_t r, bool estimate = false) {
     RayStart R;
     R.ik0 = R.ik1 = R.ik2 = 0.0;
     R.ktstart = 0;
     R.cur = -1;
     R.sg = 0;
+    R.work = 0.0f;
     R.pad = 0;
     double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
     const double kk[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
@@ -256,6 +301,7 @@ __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned c
     R.ktstart = okey(ts);
     R.cur = c;
     R.sg = sg;
+    if (estimate) R.work = estimate_work(G, oo, kk, ts, tend < tout ? tend : tout);
     return R;
 }
 

@@ -77,7 +77,7 @@ def disk_grids(hg):
     return model, out, o, k
 
 
-SHAPES = [dict(), dict(schedule=1), dict(schedule=2, block=128, smem_nodes=0), dict(block=256, smem_nodes=64),
+SHAPES = [dict(), dict(schedule=1), dict(schedule=2, block=128, smem_nodes=0), dict(schedule=3, block=256, smem_nodes=64),
           dict(schedule=1, block=64, smem_nodes=100000), dict(min_blocks=4), dict(min_blocks=4, schedule=1, block=96)]
 
 
@@ -345,7 +345,7 @@ def test_autotune_keeps_results(hg, disk_grids):
     O, K = _cuda(o), _cuda(k)
     before = _np(hg.trace_rays(grid, O, K)[0])
     cfg, ms = hg.autotune(grid, O, K)
-    assert cfg["block"] in (128, 256) and cfg["schedule"] in (1, 2) and cfg["min_blocks"] in (3, 4) and ms > 0
+    assert cfg["block"] in (128, 256) and cfg["schedule"] in (1, 2, 3) and cfg["min_blocks"] in (3, 4) and ms > 0
     after = _np(hg.trace_rays(grid, O, K)[0])
     np.testing.assert_array_equal(before, after)
 
