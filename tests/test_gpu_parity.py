@@ -390,3 +390,43 @@ def test_single_leaf_grid(hg):
     assert tree.n_leaves == 1
     o, k = synth.emission_rays(4, 500)
     _compare(hg, grid, tree, o, k)
+
+
+# ----------------------------------------------------------------------------- full-size torus + clumps grid
+# (1e7-leaf class): builder decisions sampled against the
+# oracle's node evaluation, and sampled ray sequences against the oracle walk on the same grid
+
+
+@pytest.fixture(scope="module")
+def torus_full(hg):
+    model, bp, n_rays, seed = synth.workload_torus_1e7(max_level=9)
+    H = hg.build_grid(model, bp)
+    return model, bp, H, seed
+
+
+def test_torus_full_size_builder_decisions_sampled(hg, torus_full):
+    model, bp, H, seed = torus_full
+    assert 7e6 < H.n_leaves < 1.2e7
+    rng = np.random.default_rng(1)
+    leaves = H.leaf_node[rng.choice(H.n_leaves, 300, replace=False)]
+    parent = np.full(H.n_nodes, -1, np.int64)
+    internal = np.nonzero(H.child_first >= 0)[0]
+    nch = 2
+    for c in range(nch):
+        parent[H.child_first[internal] + c] = internal
+    for nd in leaves:
+        st = oracle.node_stats(model, bp, H.level[nd], H.index[nd])
+        assert st[0] == 0.0                      # the oracle would not split this leaf either
+        assert st[1] == H.leaf_rho[H.node_leaf[nd]]  # same Monte Carlo density, bit for bit
+        p = parent[nd]
+        sp = oracle.node_stats(model, bp, H.level[p], H.index[p])
+        assert sp[0] == 1.0                      # and it would split the parent
+
+
+def test_torus_full_size_sequences_sampled(hg, torus_full):
+    model, bp, H, seed = torus_full
+    grid = hg.load_grid(H)
+    tree = oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho)
+    o, k = synth.emission_rays(seed, 20000)
+    _compare(hg, grid, tree, o, k)
+    _compare(hg, grid, tree, o, k, precision="fp32k")
