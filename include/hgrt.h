@@ -196,9 +196,25 @@ typedef struct hg_trace_opts {
                             resident thread) */
     int32_t min_blocks;  /* 0 = tuned or default (3); 3 or 4 resident 256-thread blocks per SM the
                             kernel's register budget is cut for */
-    int32_t reserved;
+    int32_t split;       /* HG_SPLIT_AUTO (0), HG_SPLIT_OFF or HG_SPLIT_FORCE; see below */
     int64_t max_steps;   /* per-ray step limit; 0 = 4 * n_leaves + 64 */
 } hg_trace_opts;
+
+/* Path segments.  With schedule 3 (work-ordered queue), in hg_trace_rays,
+ * hg_trace_rays_rho and hg_tau_gradient, a path whose estimated crossings
+ * exceed 1.5 W is cut into segments of about W that separate threads walk
+ * (W = max(32, estimated total / (4 x the launch's threads)); HG_SPLIT_FORCE:
+ * W = 2, for testing).  Cuts lie at the middle of a leaf the path crosses,
+ * deep inside it, so every segment follows the whole path's cell sequence:
+ * crossing counts, statuses, emitted cells and gradients are those of the
+ * unsplit walk; tau is the sum of the segments' partial sums, which differs
+ * from the left-to-right sum only in the grouping of the additions (a few
+ * ulps).  A segment that does not end in the leaf where the next one starts
+ * would set HG_RAY_LOST; the placement rule makes that impossible.  A
+ * max_steps below the default turns splitting off. */
+#define HG_SPLIT_AUTO 0
+#define HG_SPLIT_OFF 1
+#define HG_SPLIT_FORCE 2
 
 /* tau: dev f64[n] (HG_FP64) or f32[n] (HG_FP32K).  ncross: dev i32[n],
  * number of segments with ds > 0.  ray_status: dev u8[n] or NULL.

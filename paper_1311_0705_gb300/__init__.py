@@ -78,10 +78,15 @@ class _GridInfo(C.Structure):
 
 
 class TraceOpts(C.Structure):
-    """hg_trace_opts: precision, threads per block, shared-memory tree nodes, schedule, step limit."""
+    """hg_trace_opts: precision, threads per block, shared-memory tree nodes, schedule, register budget,
+    path splitting, step limit."""
     _fields_ = [("precision", C.c_int32), ("block", C.c_int32), ("smem_nodes", C.c_int32),
-                ("schedule", C.c_int32), ("min_blocks", C.c_int32), ("reserved", C.c_int32),
+                ("schedule", C.c_int32), ("min_blocks", C.c_int32), ("split", C.c_int32),
                 ("max_steps", C.c_int64)]
+
+
+SPLIT_AUTO, SPLIT_OFF, SPLIT_FORCE = 0, 1, 2
+_SPLIT = {"auto": SPLIT_AUTO, "off": SPLIT_OFF, "force": SPLIT_FORCE, 0: 0, 1: 1, 2: 2}
 
 
 _V = C.c_void_p
@@ -189,13 +194,17 @@ def _model_struct(model):
     return m, table
 
 
-def _opts(precision="fp64", block=0, smem_nodes=-1, schedule=0, max_steps=0, min_blocks=0) -> TraceOpts:
+def _opts(precision="fp64", block=0, smem_nodes=-1, schedule=0, max_steps=0, min_blocks=0,
+          split="auto") -> TraceOpts:
+    """Launch options.  split: "auto" (cut long paths into segments when the queue is work-ordered),
+    "off", or "force" (cut every path of more than 3 estimated crossings; for testing)."""
     o = TraceOpts()
     o.precision = {"fp64": FP64, "fp32k": FP32K, FP64: FP64, FP32K: FP32K}[precision]
     o.block = int(block)
     o.smem_nodes = int(smem_nodes)
     o.schedule = int(schedule)
     o.min_blocks = int(min_blocks)
+    o.split = _SPLIT[split]
     o.max_steps = int(max_steps)
     return o
 

@@ -110,5 +110,5 @@ struct hg_grid {
 namespace hg {
 // implemented in trace.cu
 hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precision, int &block, int &smem_nodes,
-                       int &schedule, int &min_blocks, int64_t &max_steps);
+                       int &schedule, int &min_blocks, int64_t &max_steps, int &split);
 }  // namespace hg

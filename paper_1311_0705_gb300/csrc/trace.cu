@@ -37,6 +37,14 @@ struct TraceArgs {
     const int64_t *order;  // queue position -> ray (most work first), or NULL
     int n_smem;
     int dyn;
+    // path segments of split rays (queue positions before the rays), or NULL
+    const unsigned long long *n_seg;
+    int64_t n_seg_cap;
+    const SegStart *segs;
+    double *part_acc;
+    int32_t *part_nc;
+    int32_t *part_last;
+    uint8_t *part_st;
 };
 
 // Stage the first n nodes of the (breadth-first) node list in shared memory.
@@ -64,20 +72,31 @@ __device__ __forceinline__ int work_bucket(float w) {
     return kBuckets - 1 - (b < 0 ? 0 : (b > kBuckets - 1 ? kBuckets - 1 : b));  // 0 = most work
 }
 
+// With a non-NULL work_total the pass also adds up the rays' estimated work
+// (each rounded up to an integer, so the total does not depend on the order
+// of the additions); the split planner sizes path segments from it.
 template <int KIND>
 __global__ void __launch_bounds__(256) setup_kernel(const DevGrid G, int64_t n, const double *__restrict__ o,
                                                     const double *__restrict__ d, const double *__restrict__ smax,
                                                     RayStart *starts, int n_smem, unsigned long long *bucket_count,
-                                                    const int64_t *__restrict__ seg_off) {
+                                                    const int64_t *__restrict__ seg_off,
+                                                    unsigned long long *work_total, float *work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int hist[kBuckets];
     if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
     stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
+    unsigned long long wsum = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         RayStart R = ray_setup<KIND>(G, smem, n_smem, o, d, smax, r, bucket_count != nullptr && !seg_off);
         if (seg_off) R.work = (float)(seg_off[r + 1] - seg_off[r]);
         starts[r] = R;
+        if (work) work[r] = R.work;
         if (bucket_count) atomicAdd(&hist[work_bucket(R.work)], 1u);
+        wsum += (unsigned long long)ceilf(fmaxf(R.work, 0.0f));
+    }
+    if (work_total) {
+        for (int off = 16; off > 0; off >>= 1) wsum += __shfl_down_sync(0xffffffffu, wsum, off);
+        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(work_total, wsum);
     }
     if (bucket_count) {
         __syncthreads();
@@ -85,13 +104,238 @@ __global__ void __launch_bounds__(256) setup_kernel(const DevGrid G, int64_t n, 
     }
 }
 
+// ------------------------------------------------------------------ path segments
+//
+// A launch lasts at least as long as its longest path, walked leaf after
+// leaf by one thread.  With few rays per resident thread the planner cuts
+// each long path into segments of about W estimated crossings that
+// separate threads walk, so the cell sequence stays that of the whole
+// path:
+//   * a cut is a time t_c at which the point o + d t_c lies deep inside a
+//     leaf L: at least 2^-18 times the problem's scale from every face of L
+//     (the planner works in single precision, whose rounding is ~2^-22 of
+//     that scale, and the walk's double-precision rounding ~2^-50);
+//   * the walk of the whole path is then certainly in L at t_c: it entered
+//     L before t_c and leaves it at t_out(L) > t_c, the smallest of L's
+//     wall times in the contract's arithmetic;
+//   * the segment before the cut stops after the leaf whose exit time
+//     passes t_c -- that is L, and it records L's segment with the entry
+//     time of the whole path's walk;
+//   * the segment after the cut starts in L at time t_c, does not record L,
+//     and leaves it at t_out(L) > t_c (so the exit time is not raised to the
+//     entry time): the same exit wall, exit point and next leaf as the whole
+//     path's walk, which it follows from there on.
+// The combine pass checks that each segment stopped in the leaf the next one
+// starts in (HG_RAY_LOST otherwise) and adds the partial results in path
+// order.  tau differs from the left-to-right sum of the whole path only by
+// the grouping of the additions.
+
+constexpr int kMaxSegs = 16;
+
+struct SplitRec {
+    int64_t ray;
+    int32_t first;  // its segments are first .. first+count-1, in path order
+    int32_t count;
+};
+
+// Plan the segments of the rays whose estimated work w exceeds
+// max(64, A), A = total / T the mean work per thread of the walking launch
+// (only those can outlast the launch's bulk when the heaviest go first),
+// into K = min(16, ceil(w / W)) pieces of equal estimated work,
+// W = max(32, A / 2).  Forced: every ray of more than 3 estimated crossings,
+// W = 2.  One warp per ray, over the heavy end of the work-ordered queue:
+// every lane repeats the setup's march of the work lattice, lane j places
+// cut j (descent and depth test), and the accepted cuts are those of
+// increasing t_c in distinct leaves, in path order.  Segment slots are
+// taken with one atomic per ray; their count is bounded (sum over split
+// rays of ceil(w/W) <= total/W + total/max(64, A) <= 3 T, or 16 n when
+// forced), so seg_cap is never reached -- if it were, the ray would stay
+// whole and the slots taken would be marked empty.
+constexpr int kPlanWarps = 8;  // warps per 256-thread block
+
+template <int KIND>
+__global__ void __launch_bounds__(256) split_kernel(const DevGrid G, int64_t n, const double *__restrict__ o,
+                                                    const double *__restrict__ d, const double *__restrict__ smax,
+                                                    RayStart *starts, int n_smem, const unsigned long long *work_total,
+                                                    const unsigned long long *bucket_count,
+                                                    const int64_t *__restrict__ order, int64_t threads, int force,
+                                                    SegStart *segs, int64_t seg_cap, unsigned long long *seg_count,
+                                                    SplitRec *list, unsigned long long *split_count) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int32_t s_leaf[kPlanWarps][kMaxSegs];
+    __shared__ long long s_key[kPlanWarps][kMaxSegs];
+    __shared__ long long s_ncand;
+    stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
+    if (!G.work || G.work_n <= 0) return;
+    const float A = (float)*work_total / (float)threads;
+    const float W = force ? 2.0f : fmaxf(32.0f, 0.5f * A);
+    const float thr = force ? 3.0f : fmaxf(64.0f, A);
+    if (threadIdx.x == 0) {
+        // the queue is sorted by work bucket: candidates are the buckets up to that of the threshold
+        const int bt = work_bucket(thr);
+        long long c = 0;
+        for (int b = 0; b <= bt; b++) c += (long long)bucket_count[b];
+        s_ncand = c;
+    }
+    __syncthreads();
+    const long long ncand = s_ncand;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    float dom = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) dom = fmaxf(dom, fmaxf(fabsf((float)G.dlo[a]), fabsf((float)G.dhi[a])));
+    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; q < ncand; q += nwarps) {
+        const int64_t r = order[q];
+        const RayStart R = starts[r];
+        if (R.cur < 0 || !(R.work > thr)) continue;  // uniform over the warp
+        const int K = (int)fminf((float)kMaxSegs, ceilf(R.work / W));
+        const float of[3] = {(float)o[3 * r], (float)o[3 * r + 1], (float)o[3 * r + 2]};
+        const float kf[3] = {(float)d[3 * r], (float)d[3 * r + 1], (float)d[3 * r + 2]};
+        const uint32_t sg = R.sg & 0x3fu;
+        // the walked interval as the setup's march took it: entry time to the domain exit or s_max
+        const float ts = (float)kdouble(R.ktstart);
+        const float tend = R.t1;
+        // cuts stay clear of both ends of the path
+        const float lo_t = ts + (tend - ts) * 0x1p-10f, hi_t = tend - (tend - ts) * 0x1p-10f;
+        // cut time of this lane: where the estimated work reaches (lane + 1) / K of the total
+        const float target = R.work * (float)(lane + 1) / (float)K;
+        float tc = 0.0f;
+        bool found = false;
+        work_march(G, of, kf, ts, tend, [&](float t, float tn, float rate, float e) {
+            if (!found && rate > 0.0f && e + rate * (tn - t) >= target) {
+                tc = t + (target - e) / rate;
+                found = true;
+            }
+        });
+        // the leaf containing o + d t_c, and whether the point lies deep inside it
+        bool ok = false;
+        int32_t Lid = -1;
+        if (lane < K - 1 && found && tc > lo_t && tc < hi_t) {
+            long long q3[3], qm[3], qp[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float x = of[a] + kf[a] * tc;
+                const float m = (fabsf(of[a]) + fabsf(kf[a] * tc) + dom) * 0x1p-18f;
+                q3[a] = f32_key(x);
+                qm[a] = f32_key(x - m);
+                qp[a] = f32_key(x + m);
+            }
+            if (in_axis(q3[0], G.klo[0], G.khi[0], dpos(sg, 0), dneg(sg, 0), true) &&
+                in_axis(q3[1], G.klo[1], G.khi[1], dpos(sg, 1), dneg(sg, 1), true) &&
+                in_axis(q3[2], G.klo[2], G.khi[2], dpos(sg, 2), dneg(sg, 2), true))
+                Lid = descend<KIND>(G, smem, n_smem, q3[0], q3[1], q3[2], sg);
+            if (Lid >= 0) {
+                Leaf L;
+                load_leaf(G.rec, Lid, L);
+                ok = true;
+#pragma unroll
+                for (int a = 0; a < 3; a++) ok = ok && qm[a] >= L.lo(a) && qp[a] <= L.hi(a);
+            }
+        }
+        // accept cuts in path order: increasing t_c, a leaf different from the previous cut's
+        int ncut = 0;
+        float tprev = ts;
+        int32_t prev_leaf = R.cur;
+        for (int j = 0; j < K - 1; j++) {
+            const bool okj = __shfl_sync(0xffffffffu, ok, j);
+            const float tj = __shfl_sync(0xffffffffu, tc, j);
+            const int32_t Lj = __shfl_sync(0xffffffffu, Lid, j);
+            if (okj && tj > tprev && Lj != prev_leaf) {
+                if (lane == j) {
+                    s_leaf[wib][ncut] = Lid;
+                    s_key[wib][ncut] = f32_key(tc);
+                }
+                ncut++;
+                tprev = tj;
+                prev_leaf = Lj;
+            }
+        }
+        __syncwarp();
+        if (ncut == 0) continue;
+        const int nseg = ncut + 1;
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(seg_count, (unsigned long long)nseg);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (first + (unsigned long long)nseg > (unsigned long long)seg_cap) {
+            for (unsigned long long s = first + lane; s < (unsigned long long)seg_cap; s += 32) {
+                SegStart E;
+                E.ktstart = 0;
+                E.ktstop = KEY_INF;
+                E.ray = r;
+                E.cur = -1;
+                E.sg = 0;
+                segs[s] = E;
+            }
+            continue;
+        }
+        if (lane < nseg) {
+            SegStart E;
+            E.ktstart = lane == 0 ? R.ktstart : s_key[wib][lane - 1];
+            E.ktstop = lane < ncut ? s_key[wib][lane] : KEY_INF;
+            E.ray = r;
+            E.cur = lane == 0 ? R.cur : s_leaf[wib][lane - 1];
+            E.sg = sg | (lane == 0 ? 0u : SG_SKIP_FIRST);
+            segs[first + lane] = E;
+        }
+        if (lane == 0) {
+            const unsigned long long i = atomicAdd(split_count, 1ULL);
+            SplitRec rec;
+            rec.ray = r;
+            rec.first = (int32_t)first;
+            rec.count = nseg;
+            list[i] = rec;
+            starts[r].sg = R.sg | SG_SPLIT;
+        }
+        __syncwarp();
+    }
+}
+
+// Results of the split rays from their segments' partial results.
+template <int MODE, int PREC>
+__global__ void __launch_bounds__(256) combine_kernel(const SplitRec *__restrict__ list,
+                                                      const unsigned long long *split_count,
+                                                      const SegStart *__restrict__ segs,
+                                                      const double *__restrict__ part_acc,
+                                                      const int32_t *__restrict__ part_nc,
+                                                      const int32_t *__restrict__ part_last,
+                                                      const uint8_t *__restrict__ part_st, double kappa, void *tau,
+                                                      int32_t *ncross, uint8_t *status) {
+    const int64_t m = (int64_t)*split_count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const SplitRec rec = list[i];
+        double acc = 0.0;
+        int32_t nc = 0;
+        uint32_t st = 0;
+        for (int j = 0; j < rec.count; j++) {
+            const int64_t s = rec.first + j;
+            if (MODE == MODE_TAU) {
+                acc += part_acc[s];
+                nc += part_nc[s];
+            }
+            st |= part_st[s];
+            if (j + 1 < rec.count && part_last[s] != segs[s + 1].cur) st |= HG_RAY_LOST;
+        }
+        if (MODE == MODE_TAU) {
+            if (PREC == HG_FP64)
+                static_cast<double *>(tau)[rec.ray] = kappa * acc;
+            else
+                static_cast<float *>(tau)[rec.ray] = (float)acc;
+            ncross[rec.ray] = nc;
+        }
+        if (status) status[rec.ray] = (uint8_t)st;
+    }
+}
+
 // Queue order from the bucket counts: ray r goes to the next free slot of
-// its bucket (lanes of a warp with the same bucket share one atomic; the
-// order inside a bucket is arbitrary and results do not depend on it).
-__global__ void __launch_bounds__(256) order_kernel(int64_t n, const RayStart *__restrict__ starts,
+// its bucket.  Each block ranks a chunk of rays in shared memory and takes
+// one global slot range per bucket; the order inside a bucket is arbitrary
+// and results do not depend on it.
+__global__ void __launch_bounds__(256) order_kernel(int64_t n, const float *__restrict__ work,
                                                     const unsigned long long *bucket_count,
                                                     unsigned long long *bucket_fill, int64_t *order) {
     __shared__ unsigned long long base[kBuckets];
+    __shared__ unsigned long long gbase[kBuckets];
+    __shared__ unsigned int hist[kBuckets];
     if (threadIdx.x == 0) {
         unsigned long long acc = 0;
         for (int b = 0; b < kBuckets; b++) {
@@ -99,17 +343,22 @@ __global__ void __launch_bounds__(256) order_kernel(int64_t n, const RayStart *_
             acc += bucket_count[b];
         }
     }
-    __syncthreads();
-    const unsigned lane = threadIdx.x & 31u;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        const int b = work_bucket(starts[r].work);
-        const unsigned mask = __match_any_sync(__activemask(), b);
-        const int leader = __ffs(mask) - 1;
-        const unsigned rank = __popc(mask & ((1u << lane) - 1u));
-        unsigned long long slot = 0;
-        if ((int)lane == leader) slot = atomicAdd(&bucket_fill[b], (unsigned long long)__popc(mask));
-        slot = __shfl_sync(mask, slot, leader);
-        order[base[b] + slot + rank] = r;
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < n; c0 += (int64_t)gridDim.x * blockDim.x) {
+        if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t r = c0 + threadIdx.x;
+        int b = 0;
+        unsigned rank = 0;
+        if (r < n) {
+            b = work_bucket(work[r]);
+            rank = atomicAdd(&hist[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kBuckets && hist[threadIdx.x])
+            gbase[threadIdx.x] = atomicAdd(&bucket_fill[threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+        __syncthreads();
+        if (r < n) order[base[b] + gbase[b] + rank] = r;
+        __syncthreads();
     }
 }
 
@@ -122,6 +371,7 @@ struct GridRays {
     int64_t stride;
     unsigned long long *counter;
     const int64_t *order;
+    int64_t n_seg;  // queue positions 0 .. n_seg-1 are path segments (items n + s)
     int32_t max_steps;
     bool dyn;
     __device__ __forceinline__ bool next(int64_t &ray, const DevGrid *&g, int32_t &ms) {
@@ -132,9 +382,14 @@ struct GridRays {
             unsigned long long base = 0;
             if (grp.thread_rank() == 0) base = atomicAdd(counter, (unsigned long long)grp.size());
             base = grp.shfl(base, 0);
-            ray = (int64_t)(base + grp.thread_rank());
-            if (ray < n && order) ray = order[ray];
-            return ray < n;
+            int64_t pos = (int64_t)(base + grp.thread_rank());
+            if (pos < n_seg) {
+                ray = n + pos;
+                return true;
+            }
+            pos -= n_seg;
+            ray = (pos < n && order) ? order[pos] : pos;
+            return pos < n;
         }
         ray = cursor;
         cursor += stride;
@@ -161,6 +416,11 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     src.order = A.order;
     src.max_steps = (int32_t)(A.max_steps < 0x7fffffff ? A.max_steps : 0x7fffffff);
     src.dyn = A.dyn != 0;
+    src.n_seg = 0;
+    if (A.n_seg && src.dyn) {
+        const unsigned long long c = *A.n_seg;
+        src.n_seg = (int64_t)(c < (unsigned long long)A.n_seg_cap ? c : (unsigned long long)A.n_seg_cap);
+    }
     WalkIO io;
     io.o = A.o;
     io.d = A.d;
@@ -177,6 +437,12 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.w = A.w;
     io.grad = A.grad;
     io.rho_ext = A.rho_ext;
+    io.n_rays = A.n;
+    io.segs = A.segs;
+    io.part_acc = A.part_acc;
+    io.part_nc = A.part_nc;
+    io.part_last = A.part_last;
+    io.part_st = A.part_st;
     walk_loop<KIND, MODE, PREC>(src, io, smem, A.n_smem);
 }
 
@@ -212,7 +478,7 @@ int sm_count() {
 // Default launch shape: 256 threads, the top 2048 k-d nodes (32 KB) or
 // 1024 octree nodes (32 KB) in shared memory, persistent dynamic schedule.
 hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precision, int &block, int &smem_nodes,
-                       int &schedule, int &min_blocks, int64_t &max_steps) {
+                       int &schedule, int &min_blocks, int64_t &max_steps, int &split) {
     precision = opts ? opts->precision : HG_FP64;
     if (precision != HG_FP64 && precision != HG_FP32K) {
         set_error("precision must be HG_FP64 or HG_FP32K");
@@ -225,6 +491,13 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
     schedule = (opts && opts->schedule > 0) ? opts->schedule : (T.valid ? T.schedule : 0);
     min_blocks = (opts && opts->min_blocks > 0) ? opts->min_blocks : (T.valid ? T.min_blocks : 3);
     max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 4 * g->d.n_leaves + 64;
+    split = opts ? opts->split : HG_SPLIT_AUTO;
+    if (split < HG_SPLIT_AUTO || split > HG_SPLIT_FORCE) {
+        set_error("split must be HG_SPLIT_AUTO, HG_SPLIT_OFF or HG_SPLIT_FORCE");
+        return HG_EINVAL;
+    }
+    // a step limit below the default could end a whole path but not its segments
+    if (max_steps < 4 * g->d.n_leaves + 64) split = HG_SPLIT_OFF;
     if (block < 32 || block > 256 || block % 32) {
         set_error("block must be a multiple of 32 in 32..256");
         return HG_EINVAL;
@@ -244,7 +517,7 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
 }
 
 hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int block, int smem_nodes, int schedule,
-                       int min_blocks, cudaStream_t stream) {
+                       int min_blocks, int split, cudaStream_t stream) {
     if (A.n == 0) return HG_OK;
     KernelFn k = pick_kernel(g->d.kind, mode, prec, min_blocks);
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
@@ -259,6 +532,8 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
                                              200 * 1024);
         cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(split_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(split_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
@@ -270,25 +545,55 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
     int64_t blocks = (int64_t)per_sm * sm_count();
     const int64_t need = (A.n + block - 1) / block;
     if (blocks > need) blocks = need;
+    const int64_t threads = blocks * block;
     // auto schedule: order by estimated work only when each resident thread
     // gets few paths (then the heaviest paths would otherwise set the end)
-    if (schedule == 0) schedule = (A.n < 48 * blocks * block) ? 3 : 2;
+    if (schedule == 0) schedule = (A.n < 48 * threads) ? 3 : 2;
     A.n_smem = smem_nodes;
     A.dyn = (schedule >= 2);
     const bool ordered = (schedule == 3);
-    // setup pass into a scratch array of start records
-    // scratch: start records, and for the dynamic schedule the work-ordered
-    // queue with its bucket counters
-    const size_t start_bytes = ((size_t)A.n * sizeof(RayStart) + 255) / 256 * 256;
-    const size_t order_bytes = ordered ? ((size_t)A.n * sizeof(int64_t) + 255) / 256 * 256 : 0;
-    const size_t count_bytes = ordered ? 2 * kBuckets * sizeof(unsigned long long) : 0;
+    // long paths are cut into segments in the modes whose per-ray results add up
+    const bool splitting = ordered && split != HG_SPLIT_OFF && (mode == MODE_TAU || mode == MODE_ADJ) && g->d.work;
+    const int64_t seg_cap =
+        splitting ? std::min<int64_t>((split == HG_SPLIT_FORCE ? 16 * A.n : 3 * threads) + 1024, 16 * A.n) : 0;
+    // scratch: start records; for the ordered schedule the queue and its
+    // counters (bucket counts and fills, work total, segment and split-ray
+    // counts); for splitting the segment records, partial results and the
+    // list of split rays
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t start_bytes = al((size_t)A.n * sizeof(RayStart));
+    const size_t order_bytes = ordered ? al((size_t)A.n * sizeof(int64_t)) : 0;
+    const size_t work_bytes = ordered ? al((size_t)A.n * sizeof(float)) : 0;
+    const size_t count_bytes = ordered ? al((2 * kBuckets + 3) * sizeof(unsigned long long)) : 0;
+    const size_t seg_bytes = al((size_t)seg_cap * sizeof(SegStart));
+    const size_t acc_bytes = al((size_t)seg_cap * sizeof(double));
+    const size_t i32_bytes = al((size_t)seg_cap * sizeof(int32_t));
+    const size_t u8_bytes = al((size_t)seg_cap);
+    const size_t list_bytes = al((size_t)(seg_cap / 2) * sizeof(SplitRec));
+    const size_t total_bytes = start_bytes + order_bytes + work_bytes + count_bytes + seg_bytes + acc_bytes +
+                               2 * i32_bytes + u8_bytes + list_bytes;
     unsigned char *scratch = nullptr;
-    e = cudaMallocAsync((void **)&scratch, start_bytes + order_bytes + count_bytes, stream);
+    e = cudaMallocAsync((void **)&scratch, total_bytes, stream);
     if (e != cudaSuccess) return cuda_err(e, "ray start scratch");
-    RayStart *starts = reinterpret_cast<RayStart *>(scratch);
-    int64_t *order = ordered ? reinterpret_cast<int64_t *>(scratch + start_bytes) : nullptr;
-    unsigned long long *counts =
-        ordered ? reinterpret_cast<unsigned long long *>(scratch + start_bytes + order_bytes) : nullptr;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        unsigned char *p = b ? scratch + off : nullptr;
+        off += b;
+        return p;
+    };
+    RayStart *starts = reinterpret_cast<RayStart *>(take(start_bytes));
+    int64_t *order = reinterpret_cast<int64_t *>(take(order_bytes));
+    float *work = reinterpret_cast<float *>(take(work_bytes));
+    unsigned long long *counts = reinterpret_cast<unsigned long long *>(take(count_bytes));
+    SegStart *segs = reinterpret_cast<SegStart *>(take(seg_bytes));
+    A.part_acc = reinterpret_cast<double *>(take(acc_bytes));
+    A.part_nc = reinterpret_cast<int32_t *>(take(i32_bytes));
+    A.part_last = reinterpret_cast<int32_t *>(take(i32_bytes));
+    A.part_st = reinterpret_cast<uint8_t *>(take(u8_bytes));
+    SplitRec *list = reinterpret_cast<SplitRec *>(take(list_bytes));
+    unsigned long long *work_total = counts ? counts + 2 * kBuckets : nullptr;
+    unsigned long long *seg_count = counts ? counts + 2 * kBuckets + 1 : nullptr;
+    unsigned long long *split_count = counts ? counts + 2 * kBuckets + 2 : nullptr;
     if (counts) {
         e = cudaMemsetAsync(counts, 0, count_bytes, stream);
         if (e != cudaSuccess) {
@@ -296,21 +601,36 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
             return cuda_err(e, "scratch reset");
         }
     }
+    const int64_t sblocks = std::min<int64_t>((A.n + 255) / 256, (int64_t)sm_count() * 8);
     {
         // the fill pass knows each ray's exact crossing count from its offsets
         const int64_t *exact = (mode == MODE_FILL) ? A.seg_off : nullptr;
-        const int64_t sblocks = std::min<int64_t>((A.n + 255) / 256, (int64_t)sm_count() * 8);
         if (g->d.kind == HG_KDTREE)
-            setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, A.n, A.o, A.d, A.smax, starts,
-                                                                             smem_nodes, counts, exact);
+            setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
+                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, counts, exact, work_total, work);
         else
-            setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, A.n, A.o, A.d, A.smax, starts,
-                                                                             smem_nodes, counts, exact);
+            setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
+                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, counts, exact, work_total, work);
         note_launches(1);
         if (order) {
-            order_kernel<<<(unsigned)sblocks, 256, 0, stream>>>(A.n, starts, counts, counts + kBuckets, order);
+            order_kernel<<<(unsigned)sblocks, 256, 0, stream>>>(A.n, work, counts, counts + kBuckets, order);
             note_launches(1);
         }
+    }
+    if (splitting) {
+        const int force = split == HG_SPLIT_FORCE ? 1 : 0;
+        if (g->d.kind == HG_KDTREE)
+            split_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
+                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, work_total, counts, order, threads, force, segs,
+                seg_cap, seg_count, list, split_count);
+        else
+            split_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
+                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, work_total, counts, order, threads, force, segs,
+                seg_cap, seg_count, list, split_count);
+        note_launches(1);
+        A.n_seg = seg_count;
+        A.n_seg_cap = seg_cap;
+        A.segs = segs;
     }
     A.starts = starts;
     A.order = order;
@@ -332,6 +652,26 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
     k<<<(unsigned)blocks, block, smem, stream>>>(A);
     e = cudaGetLastError();
     note_launches(1);
+    if (e == cudaSuccess && splitting) {
+        const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((seg_cap / 2 + 255) / 256,
+                                                                                 (int64_t)sm_count() * 4));
+        if (mode == MODE_TAU) {
+            if (prec == HG_FP64)
+                combine_kernel<MODE_TAU, HG_FP64><<<cblocks, 256, 0, stream>>>(
+                    list, split_count, segs, A.part_acc, A.part_nc, A.part_last, A.part_st, A.kappa, A.tau, A.ncross,
+                    A.status);
+            else
+                combine_kernel<MODE_TAU, HG_FP32K><<<cblocks, 256, 0, stream>>>(
+                    list, split_count, segs, A.part_acc, A.part_nc, A.part_last, A.part_st, A.kappa, A.tau, A.ncross,
+                    A.status);
+        } else {
+            combine_kernel<MODE_ADJ, 0><<<cblocks, 256, 0, stream>>>(list, split_count, segs, A.part_acc, A.part_nc,
+                                                                   A.part_last, A.part_st, A.kappa, nullptr,
+                                                                   nullptr, A.status);
+        }
+        e = cudaGetLastError();
+        note_launches(1);
+    }
     if (ctr) cudaFreeAsync(ctr, stream);
     cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_err(e, "trace launch");
@@ -482,9 +822,9 @@ extern "C" hg_status hg_trace_rays(const hg_grid *g, int64_t n, const double *o,
         set_error("hg_trace_rays: tau and ncross are required");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule, min_blocks;
+    int prec, block, smem_nodes, schedule, min_blocks, split;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps, split)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -496,7 +836,7 @@ extern "C" hg_status hg_trace_rays(const hg_grid *g, int64_t n, const double *o,
     A.ncross = ncross;
     A.status = ray_status;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
+    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, min_blocks, split, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double *o, const double *d,
@@ -509,9 +849,9 @@ extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double
         set_error("hg_trace_rays_rho: rho, tau and ncross are required");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule, min_blocks;
+    int prec, block, smem_nodes, schedule, min_blocks, split;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps, split)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -524,7 +864,7 @@ extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double
     A.ncross = ncross;
     A.status = ray_status;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
+    return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, min_blocks, split, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o, const double *d,
@@ -537,9 +877,9 @@ extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o,
         set_error("hg_trace_fill: bad segment arrays");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule, min_blocks;
+    int prec, block, smem_nodes, schedule, min_blocks, split;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps, split)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -552,7 +892,7 @@ extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o,
     A.seg_cap = seg_capacity;
     A.status = ray_status;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_FILL, prec, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
+    return launch_trace(g, MODE_FILL, prec, A, block, smem_nodes, schedule, min_blocks, split, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *o, const double *d,
@@ -568,9 +908,9 @@ extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *
         set_error("hg_tau_gradient: grad_precision must be 0 (f64) or 1 (f32)");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule, min_blocks;
+    int prec, block, smem_nodes, schedule, min_blocks, split;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps, split)) != HG_OK) return st;
     TraceArgs A{};
     A.G = g->d;
     A.n = n;
@@ -581,7 +921,8 @@ extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *
     A.w = w;
     A.grad = grad_rho;
     A.max_steps = max_steps;
-    return launch_trace(g, MODE_ADJ, grad_precision, A, block, smem_nodes, schedule, min_blocks, (cudaStream_t)stream);
+    return launch_trace(g, MODE_ADJ, grad_precision, A, block, smem_nodes, schedule, min_blocks, split,
+                        (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_sample_density(const hg_grid *g, int64_t n, const double *pts, int32_t *cell, double *rho,
@@ -678,9 +1019,9 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
         set_error("tau and ncross are required");
         return HG_EINVAL;
     }
-    int prec, block, smem_nodes, schedule, min_blocks;
+    int prec, block, smem_nodes, schedule, min_blocks, split;
     int64_t max_steps;
-    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps)) != HG_OK) return st;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps, split)) != HG_OK) return st;
     if (n == 0) return HG_OK;
     TraceArgs A{};
     A.G = g->d;
@@ -720,10 +1061,10 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
     const int64_t sblocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     if (g->d.kind == HG_KDTREE)
         setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes,
-                                                                         nullptr, nullptr);
+                                                                         nullptr, nullptr, nullptr, nullptr);
     else
         setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes,
-                                                                         nullptr, nullptr);
+                                                                         nullptr, nullptr, nullptr, nullptr);
     k<<<(unsigned)blocks, block, smem, stream>>>(A);
     note_launches(2);
     e = cudaGetLastError();

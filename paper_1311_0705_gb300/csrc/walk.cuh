@@ -154,14 +154,19 @@ __device__ __forceinline__ int32_t descend(const DevGrid &G, const unsigned char
 // Per-ray walking state.
 struct RayState {
     double o0, o1, o2, k0, k1, k2, ik0, ik1, ik2;
-    long long ktend;  // key of the path end (KEY_INF: walk to the domain exit)
-    long long ktcur;  // key of the current time
+    long long ktend;   // key of the path end (KEY_INF: walk to the domain exit)
+    long long ktstop;  // a path segment ends after the leaf whose exit time passes this (KEY_INF: none)
+    long long ktcur;   // key of the current time
     uint32_t sg;      // direction sign bits
     int32_t cur;
     int32_t steps;
 };
 
-enum { WALK_GO = 0, WALK_END = 1 };
+enum { WALK_GO = 0, WALK_END = 1, WALK_SKIP = 2 };
+
+// Flag bits above the six direction-sign bits of a ray's sg word.
+constexpr uint32_t SG_SKIP_FIRST = 1u << 6;  // a path segment: its first leaf belongs to the segment before
+constexpr uint32_t SG_SPLIT = 1u << 7;       // the ray is walked as path segments (start record only)
 
 // Start state of a ray, written by the setup pass and read when a walking
 // thread takes the ray: 48 bytes, three 16-byte loads.
@@ -171,58 +176,102 @@ struct alignas(16) RayStart {
     int32_t cur;           // first leaf, or -1 when the ray does not walk
     uint32_t sg;           // direction sign bits | status bits << 8
     float work;            // estimated number of crossings (orders the queue)
-    int32_t pad;
+    float t1;              // end of the estimate's march (domain exit or s_max, single precision)
 };
 static_assert(sizeof(RayStart) == 48 && offsetof(RayStart, ktstart) == 24 && offsetof(RayStart, cur) == 32 &&
                   offsetof(RayStart, sg) == 36,
               "ray_resume reads the start record as two double2 and one int4");
 
-// Estimated number of leaf crossings of the path o + t d, t in [t0, t1]: a
-// single-precision march through the coarse lattice of expected crossings
-// per unit length.  Only orders the work; it never affects a result.
-__device__ __forceinline__ float estimate_work(const DevGrid &G, const double *o, const double *d, double t0,
-                                               double t1) {
+// Start record of one segment of a long path (written by the split planner):
+// the leaf it starts in and the time it enters it, and the time after which
+// it stops.  32 bytes, two 16-byte loads; 1/d comes from the ray's RayStart.
+struct alignas(16) SegStart {
+    long long ktstart;  // key of the entry time into the first leaf
+    long long ktstop;   // stop after the leaf whose exit time passes this (KEY_INF: walk to the end)
+    int64_t ray;
+    int32_t cur;        // first leaf
+    uint32_t sg;        // direction sign bits | SG_SKIP_FIRST
+};
+static_assert(sizeof(SegStart) == 32 && offsetof(SegStart, ray) == 16,
+              "seg_resume reads the segment record as two longlong2");
+
+// Key (okey) of the double equal to the FP32 value with bits fb; subnormal
+// FP32 values map to zero's key.  Integer operations only.
+__device__ __forceinline__ long long f32_key(float f) {
+    const uint32_t fb = __float_as_uint(f);
+    const uint32_t e = (fb >> 23) & 0xffu;
+    if (e == 0u) return 0LL;
+    const unsigned long long mag = e == 0xffu ? 0x7ff0000000000000ULL
+                                               : ((unsigned long long)(e + 896u) << 52) |
+                                                     ((unsigned long long)(fb & 0x7fffffu) << 29);
+    return (fb >> 31) ? -(long long)mag : (long long)mag;
+}
+
+// March of the path o + t k, t in [t0, t1], through the coarse work
+// lattice (expected crossings per unit length, G.work): a 3-D DDA
+// (Amanatides & Woo, 1987) in single precision.  Calls f(t, tn, rate, e)
+// for every lattice cell the path crosses, [t, tn] being the part inside
+// it and e the work before it; returns the total work.  It only orders and
+// cuts the work; it never affects a result.
+template <class F>
+__device__ __forceinline__ float work_march(const DevGrid &G, const float *o, const float *k, float t0, float t1,
+                                            F &&f) {
     const int N = G.work_n;
     if (!G.work || N <= 0 || !(t1 > t0)) return 0.0f;
-    float sc[3], p[3], k[3];
-    int c[3];
+    float tmax[3], tdel[3];
+    int c[3], step[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        sc[a] = (float)N / (float)(G.dhi[a] - G.dlo[a]);
-        k[a] = (float)d[a] * sc[a];  // lattice units per unit t
-        p[a] = (float)((o[a] + d[a] * t0) - G.dlo[a]) * sc[a];
-        int ci = (int)floorf(p[a]);
-        c[a] = ci < 0 ? 0 : (ci > N - 1 ? N - 1 : ci);
-    }
-    float t = (float)t0;
-    const float tend = (float)t1;
-    float e = 0.0f;
-    for (int it = 0; it < 3 * N + 3 && t < tend; it++) {
-        float tn = tend;
-        int ax = -1;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (k[a] == 0.0f) continue;
-            const float wall = (float)(k[a] > 0.0f ? c[a] + 1 : c[a]);
-            const float ta = t + (wall - (p[a] + k[a] * (t - (float)t0))) / k[a];
-            if (ta < tn) {
-                tn = ta;
-                ax = a;
-            }
+        const float lo = (float)G.dlo[a];
+        const float sc = (float)N / ((float)G.dhi[a] - lo);
+        const float ka = k[a] * sc;  // lattice units per unit t
+        const float p = (o[a] + k[a] * t0 - lo) * sc;
+        int ci = (int)floorf(p);
+        ci = ci < 0 ? 0 : (ci > N - 1 ? N - 1 : ci);
+        c[a] = ci;
+        if (ka > 0.0f) {
+            tdel[a] = 1.0f / ka;
+            tmax[a] = t0 + ((float)(ci + 1) - p) * tdel[a];
+            step[a] = 1;
+        } else if (ka < 0.0f) {
+            tdel[a] = -1.0f / ka;
+            tmax[a] = t0 + (p - (float)ci) * tdel[a];
+            step[a] = -1;
+        } else {
+            tdel[a] = 0.0f;
+            tmax[a] = CUDART_INF_F;
+            step[a] = 0;
         }
+    }
+    float t = t0;
+    float e = 0.0f;
+    for (int it = 0; it < 3 * N + 3; it++) {
+        const int ax = (tmax[0] <= tmax[1]) ? (tmax[0] <= tmax[2] ? 0 : 2) : (tmax[1] <= tmax[2] ? 1 : 2);
+        float tn = fminf(tmax[ax], t1);
         if (tn < t) tn = t;
-        e += __ldg(G.work + c[0] + N * (c[1] + N * c[2])) * (tn - t);
+        const float rate = __ldg(G.work + c[0] + N * (c[1] + N * c[2]));
+        f(t, tn, rate, e);
+        e += rate * (tn - t);
         t = tn;
-        if (ax < 0) break;
-        c[ax] += k[ax] > 0.0f ? 1 : -1;
+        if (!(tmax[ax] < t1)) break;
+        c[ax] += step[ax];
         if (c[ax] < 0 || c[ax] >= N) break;
+        tmax[ax] += tdel[ax];
     }
     return e;
 }
 
+// Bit tests on doubles (integer operations: the FP64 pipe is scarce).
+__device__ __forceinline__ bool dfinite(double x) { return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff; }
+__device__ __forceinline__ bool dzero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool dgt0(double x) { return __double_as_longlong(x) > 0; }  // x > 0 (x not NaN)
+__device__ __forceinline__ bool dlt0(double x) { return __double_as_longlong(x) < 0 && !dzero(x); }
+
 // Set up a ray (the first-cell location of Sect. 2.3): checks, 1/d, clip
 // against the domain, top-down descent to the first leaf.  Runs once per
-// ray in its own pass, so it keeps plain FP64 compares.
+// ray in its own pass.  An origin strictly inside the domain (every
+// emission path) needs no clip: the contract's entry time is then 0 and
+// the start point the origin itself.
 template <int KIND>
 __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned char *snodes, int n_smem,
                                               const double *__restrict__ o, const double *__restrict__ d,
@@ -233,63 +282,82 @@ __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned c
     R.cur = -1;
     R.sg = 0;
     R.work = 0.0f;
-    R.pad = 0;
+    R.t1 = 0.0f;
     double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
     const double kk[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
     const double tend = smax ? smax[r] : CUDART_INF;
-    if (!(isfinite(oo[0]) && isfinite(oo[1]) && isfinite(oo[2]) && isfinite(kk[0]) && isfinite(kk[1]) &&
-          isfinite(kk[2])) ||
-        (kk[0] == 0.0 && kk[1] == 0.0 && kk[2] == 0.0) || isnan(tend)) {
+    const bool tend_nan = !dfinite(tend) && (__double_as_longlong(tend) << 12) != 0;
+    if (!(dfinite(oo[0]) && dfinite(oo[1]) && dfinite(oo[2]) && dfinite(kk[0]) && dfinite(kk[1]) &&
+          dfinite(kk[2])) ||
+        (dzero(kk[0]) && dzero(kk[1]) && dzero(kk[2])) || tend_nan) {
         R.sg = HG_RAY_BADINPUT << 8;
         return R;
     }
     // a signed-zero origin coordinate gives the same comparisons and sums as +0
 #pragma unroll
     for (int a = 0; a < 3; a++)
-        if (oo[a] == 0.0) oo[a] = 0.0;
+        if (dzero(oo[a])) oo[a] = 0.0;
     double ik[3];
     uint32_t sg = 0;
+    long long ko[3];
+    bool inside = true;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        ik[a] = (kk[a] != 0.0) ? 1.0 / kk[a] : 0.0;
-        sg |= (kk[a] > 0.0 ? 1u : 0u) << a;
-        sg |= (kk[a] < 0.0 ? 1u : 0u) << (3 + a);
+        ik[a] = dzero(kk[a]) ? 0.0 : 1.0 / kk[a];
+        sg |= (dgt0(kk[a]) ? 1u : 0u) << a;
+        sg |= (dlt0(kk[a]) ? 1u : 0u) << (3 + a);
+        ko[a] = okey(oo[a]);
+        inside = inside && G.klo[a] < ko[a] && ko[a] < G.khi[a];
     }
-    double ts = 0.0, tout = CUDART_INF;
-    int entry = -1;
+    double ts = 0.0;
+    long long p[3] = {ko[0], ko[1], ko[2]};
+    float t1f;
+    if (inside) {
+        // entry time 0; the path is empty only when s_max <= 0
+        if (!(okey(tend) > 0)) return R;
+        float tout = CUDART_INF_F;
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        if (kk[a] == 0.0) {
-            if (oo[a] < G.dlo[a] || oo[a] > G.dhi[a]) return R;
-            continue;
+        for (int a = 0; a < 3; a++)
+            if (!dzero(kk[a]))
+                tout = fminf(tout, ((dgt0(kk[a]) ? (float)G.dhi[a] : (float)G.dlo[a]) - (float)oo[a]) / (float)kk[a]);
+        t1f = fminf(tout, (float)tend);
+    } else {
+        double tout = CUDART_INF;
+        int entry = -1;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (dzero(kk[a])) {
+                if (ko[a] < G.klo[a] || ko[a] > G.khi[a]) return R;
+                continue;
+            }
+            const double tn = ((dgt0(kk[a]) ? G.dlo[a] : G.dhi[a]) - oo[a]) * ik[a];
+            const double tf = ((dgt0(kk[a]) ? G.dhi[a] : G.dlo[a]) - oo[a]) * ik[a];
+            if (tn > ts) {
+                ts = tn;
+                entry = a;
+            }
+            if (tf < tout) tout = tf;
         }
-        const double tn = ((kk[a] > 0.0 ? G.dlo[a] : G.dhi[a]) - oo[a]) * ik[a];
-        const double tf = ((kk[a] > 0.0 ? G.dhi[a] : G.dlo[a]) - oo[a]) * ik[a];
-        if (tn > ts) {
-            ts = tn;
-            entry = a;
+        if (!(ts < tout) || !(ts < tend)) return R;
+        if (entry >= 0) {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                double v;
+                if (a == entry) {
+                    v = dgt0(kk[a]) ? G.dlo[a] : G.dhi[a];
+                } else {
+                    v = oo[a] + kk[a] * ts;
+                    if (v < G.dlo[a]) v = G.dlo[a];
+                    if (v > G.dhi[a]) v = G.dhi[a];
+                }
+                p[a] = okey(v);
+            }
         }
-        if (tf < tout) tout = tf;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            if (!in_axis(p[a], G.klo[a], G.khi[a], dpos(sg, a), dneg(sg, a), true)) return R;
+        t1f = (float)(tend < tout ? tend : tout);
     }
-    if (!(ts < tout) || !(ts < tend)) return R;
-    long long p[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        double v;
-        if (entry < 0) {
-            v = oo[a];
-        } else if (a == entry) {
-            v = (kk[a] > 0.0) ? G.dlo[a] : G.dhi[a];
-        } else {
-            v = oo[a] + kk[a] * ts;
-            if (v < G.dlo[a]) v = G.dlo[a];
-            if (v > G.dhi[a]) v = G.dhi[a];
-        }
-        p[a] = okey(v);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-        if (!in_axis(p[a], G.klo[a], G.khi[a], dpos(sg, a), dneg(sg, a), true)) return R;
     const int32_t c = descend<KIND>(G, snodes, n_smem, p[0], p[1], p[2], sg);
     if (c < 0) {
         R.sg = HG_RAY_LOST << 8;
@@ -301,7 +369,12 @@ __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned c
     R.ktstart = okey(ts);
     R.cur = c;
     R.sg = sg;
-    if (estimate) R.work = estimate_work(G, oo, kk, ts, tend < tout ? tend : tout);
+    R.t1 = t1f;
+    if (estimate) {
+        const float of[3] = {(float)oo[0], (float)oo[1], (float)oo[2]};
+        const float kf[3] = {(float)kk[0], (float)kk[1], (float)kk[2]};
+        R.work = work_march(G, of, kf, (float)ts, t1f, [](float, float, float, float) {});
+    }
     return R;
 }
 
@@ -317,12 +390,47 @@ __device__ __forceinline__ int ray_resume(const double *__restrict__ o, const do
     // c = {cur, sg | status << 8, pad, pad}
     *st = (uint32_t)c.y >> 8;
     if (c.x < 0) return WALK_END;
+    if ((uint32_t)c.y & SG_SPLIT) return WALK_SKIP;  // its segments do the work
     S.ik0 = a.x;
     S.ik1 = a.y;
     S.ik2 = b.x;
     S.ktcur = __double_as_longlong(b.y);
     S.cur = c.x;
     S.sg = (uint32_t)c.y & 0xffu;
+    const double o0 = o[3 * r], o1 = o[3 * r + 1], o2 = o[3 * r + 2];
+    S.o0 = (o0 == 0.0) ? 0.0 : o0;
+    S.o1 = (o1 == 0.0) ? 0.0 : o1;
+    S.o2 = (o2 == 0.0) ? 0.0 : o2;
+    S.k0 = d[3 * r];
+    S.k1 = d[3 * r + 1];
+    S.k2 = d[3 * r + 2];
+    S.ktend = smax ? okey(smax[r]) : KEY_INF;
+    S.ktstop = KEY_INF;
+    S.steps = 0;
+    return WALK_GO;
+}
+
+// Take a path segment for walking: its start leaf and entry time from the
+// segment record, 1/d from the ray's start record.  *ray = the ray it is part
+// of.  Returns WALK_END for an empty record (no start leaf).
+__device__ __forceinline__ int seg_resume(const double *__restrict__ o, const double *__restrict__ d,
+                                           const double *__restrict__ smax, const RayStart *__restrict__ starts,
+                                           const SegStart *__restrict__ segs, int64_t s, RayState &S,
+                                           int64_t *ray) {
+    const longlong2 *q = reinterpret_cast<const longlong2 *>(segs + s);
+    const longlong2 a = __ldg(q), b = __ldg(q + 1);
+    const int64_t r = b.x;
+    *ray = r;
+    S.ktcur = a.x;
+    S.ktstop = a.y;
+    S.cur = (int32_t)(uint32_t)((unsigned long long)b.y & 0xffffffffULL);
+    S.sg = (uint32_t)((unsigned long long)b.y >> 32);
+    if (S.cur < 0) return WALK_END;
+    const double2 *p = reinterpret_cast<const double2 *>(starts + r);
+    const double2 i01 = __ldg(p), i2 = __ldg(p + 1);
+    S.ik0 = i01.x;
+    S.ik1 = i01.y;
+    S.ik2 = i2.x;
     const double o0 = o[3 * r], o1 = o[3 * r + 1], o2 = o[3 * r + 2];
     S.o0 = (o0 == 0.0) ? 0.0 : o0;
     S.o1 = (o1 == 0.0) ? 0.0 : o1;
@@ -345,10 +453,12 @@ __device__ __forceinline__ long long wall_time(bool pos, bool neg, long long lo,
 // Exit-wall test of the current leaf (the step the paper calls the most
 // important, Sect. 2.3).  Sets *ds (0: nothing to record) and *ax (-1 when
 // the path ends inside the leaf).  Returns WALK_END when the walk stops
-// after this leaf's segment, WALK_GO when ray_advance should follow.
-__device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Leaf &L, double *ds, int *ax_out,
-                                        double *tex_out, uint32_t *st) {
+// after this leaf's segment (the path ends, leaves the domain, or a path
+// segment reaches its stop time), WALK_GO when the next leaf follows.
+__device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Leaf &L, double *ds, bool *rec,
+                                        int *ax_out, double *tex_out, uint32_t *st) {
     *ds = 0.0;
+    *rec = false;
     *ax_out = -1;
     if (S.steps >= max_steps) {
         *st = HG_RAY_STEPLIMIT;
@@ -369,10 +479,11 @@ __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Le
     if (kt < S.ktcur) kt = S.ktcur;
     const double tex = kdouble(kt);
     *ds = tex - kdouble(S.ktcur);
+    *rec = kt != S.ktcur;  // ds != 0 (equal keys are equal times)
     S.ktcur = kt;
     *ax_out = ax;
     *tex_out = tex;
-    if (ax < 0) return WALK_END;
+    if (ax < 0 || kt > S.ktstop) return WALK_END;
     if (L.first(2 * ax + (dpos(sg, ax) ? 1 : 0)) < 0) return WALK_END;  // exit wall on the domain boundary
     return WALK_GO;
 }
@@ -491,6 +602,14 @@ struct WalkIO {
     const float *w;
     void *grad;
     const double *rho_ext;  // densities replacing the grid's own (MODE_TAU), or NULL
+    // Path segments: queue items n_rays + s are segment s of a split ray.
+    // Each writes its partial results at index s; a combine pass sums them.
+    int64_t n_rays = 0x7fffffffffffffffLL;
+    const SegStart *segs = nullptr;
+    double *part_acc = nullptr;    // partial sum of rho*ds (FP64) or the Kahan sum (FP32K)
+    int32_t *part_nc = nullptr;    // partial crossing count
+    int32_t *part_last = nullptr;  // leaf the segment stopped in
+    uint8_t *part_st = nullptr;    // partial status bits
 };
 
 // The walking loop of one thread.  Each iteration loads exactly one leaf
@@ -498,7 +617,8 @@ struct WalkIO {
 // head, or the next tail entry after a miss), or the leaf a top-down
 // search found -- so a lane that missed the list head costs its warp one
 // more iteration instead of a chain of dependent loads inside one.
-// Src hands out rays: bool next(int64_t &ray, const DevGrid *&G, int32_t &max_steps).
+// Src hands out rays: bool next(int64_t &ray, const DevGrid *&G, int32_t &max_steps);
+// an item ray >= io.n_rays is path segment ray - io.n_rays of a split ray.
 //   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
 //   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
 template <int KIND, int MODE, int PREC, class Src>
@@ -525,10 +645,21 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             acc32 = 0.0f;
             comp32 = 0.0f;
             nc = 0;
-            if (MODE == MODE_FILL) seg_base = io.seg_off[ray];
-            if (MODE == MODE_ADJ) wk = io.kappa * (double)io.w[ray];
             have = true;
-            if (ray_resume(io.o, io.d, io.smax, io.starts, ray, S, &st) == WALK_END) goto finish;
+            int64_t r = ray;
+            int rs = WALK_GO;
+            st = 0;
+            if (ray >= io.n_rays)
+                rs = seg_resume(io.o, io.d, io.smax, io.starts, io.segs, ray - io.n_rays, S, &r);
+            else
+                rs = ray_resume(io.o, io.d, io.smax, io.starts, ray, S, &st);
+            if (rs == WALK_SKIP) {
+                have = false;
+                continue;
+            }
+            if (MODE == MODE_FILL) seg_base = io.seg_off[r];
+            if (MODE == MODE_ADJ) wk = io.kappa * (double)io.w[r];
+            if (rs == WALK_END) goto finish;
             C.id = S.cur;
             C.mode = CAND_ENTER;
         }
@@ -555,9 +686,12 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             }
             S.cur = C.id;
             double ds, tex;
+            bool rec;
             int ax;
-            const int r = ray_exit(max_steps, S, L, &ds, &ax, &tex, &st);
-            if (ds != 0.0) {
+            const int r = ray_exit(max_steps, S, L, &ds, &rec, &ax, &tex, &st);
+            const bool skip = (S.sg & SG_SKIP_FIRST) != 0;  // the segment before records this leaf
+            S.sg &= ~SG_SKIP_FIRST;
+            if (rec && !skip) {
                 if (MODE == MODE_TAU) {
                     if (PREC == HG_FP64) {
                         const double rho = io.rho_ext ? __ldg(io.rho_ext + S.cur) : L.rho;
@@ -596,7 +730,15 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             }
         }
     finish:
-        if (MODE == MODE_TAU) {
+        if (ray >= io.n_rays) {
+            const int64_t sidx = ray - io.n_rays;
+            if (MODE == MODE_TAU) {
+                io.part_acc[sidx] = (PREC == HG_FP64) ? acc : (double)acc32;
+                io.part_nc[sidx] = nc;
+            }
+            io.part_last[sidx] = S.cur;
+            io.part_st[sidx] = (uint8_t)st;
+        } else if (MODE == MODE_TAU) {
             if (PREC == HG_FP64)
                 static_cast<double *>(io.tau)[ray] = io.kappa * acc;
             else

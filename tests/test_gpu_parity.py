@@ -253,6 +253,89 @@ def test_adjoint_against_oracle_accumulation(hg, disk_grids, kind):
     assert (np.abs(g32 - g64_ref) <= gam * np.abs(g64_ref) + 1e-30).all()
 
 
+# ----------------------------------------------------------------------------- path segments
+
+def _launches(hg, fn):
+    n0 = hg.launch_count()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, hg.launch_count() - n0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32k"])
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_forced_path_segments_match_oracle(hg, disk_grids, kind, precision):
+    # every path of more than 3 estimated crossings is cut into up to 16 segments walked apart
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    O, K = _cuda(o), _cuda(k)
+    ref = oracle.trace(tree, o, k, kappa=1.3)
+    (tau, nc, st), n = _launches(hg, lambda: hg.trace_rays(grid, O, K, kappa=1.3, precision=precision,
+                                                            split="force"))
+    assert n == 5  # setup, queue order, split planner, walk, combine
+    np.testing.assert_array_equal(_np(nc), ref["ncross"])
+    np.testing.assert_array_equal(_np(st), ref["status"])
+    _check_tau(_np(tau), ref["tau"], TAU_RTOL_FP64 if precision == "fp64" else TAU_RTOL_FP32K)
+    (whole, nc1, _), n1 = _launches(hg, lambda: hg.trace_rays(grid, O, K, kappa=1.3, precision=precision,
+                                                               split="off", schedule=3))
+    assert n1 == 3
+    np.testing.assert_array_equal(_np(nc1), ref["ncross"])
+    if precision == "fp64":
+        # the same segments, summed in groups: a few ulps apart, and some rays do differ
+        _check_tau(_np(tau), _np(whole), 1e-13)
+        assert (_np(tau) != _np(whole)).any()
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_forced_segments_with_path_ends(hg, disk_grids, kind):
+    model, grids, _, _ = disk_grids
+    grid, tree, _ = grids[kind]
+    a, k, L = synth.endpoint_paths(78, 3001)
+    for frac, prec in ((1.0, "fp64"), (0.37, "fp32k"), (0.9, "fp64")):
+        smax = L * frac
+        ref = oracle.trace(tree, a, k, smax=smax, kappa=2.5)
+        tau, nc, st = hg.trace_rays(grid, _cuda(a), _cuda(k), _cuda(smax), kappa=2.5, precision=prec,
+                                    split="force")
+        np.testing.assert_array_equal(_np(nc), ref["ncross"])
+        np.testing.assert_array_equal(_np(st), ref["status"])
+        _check_tau(_np(tau), ref["tau"], TAU_RTOL_FP64 if prec == "fp64" else TAU_RTOL_FP32K)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_forced_segments_degenerate_rays(hg, kind):
+    # rays along planes, edges and through corners of a dyadic grid: cuts are only placed deep inside leaves
+    model = synth.make_dyadic(7, level=2)
+    bp = synth.BuildParams(kind=kind, delta_max=1e-3, max_level=4)
+    grid = hg.load_grid(hg.build_grid(model, bp))
+    tree = oracle.build_tree(model, bp)
+    o, k = synth.degenerate_rays(levels=4, n_random=3000, seed=kind + 11)
+    ref = oracle.trace(tree, o, k)
+    tau, nc, st = hg.trace_rays(grid, _cuda(o), _cuda(k), split="force")
+    np.testing.assert_array_equal(_np(nc), ref["ncross"])
+    np.testing.assert_array_equal(_np(st), ref["status"])
+    _check_tau(_np(tau), ref["tau"], TAU_RTOL_FP64)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_forced_segments_adjoint(hg, disk_grids, kind):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    w = synth.adjoint_weights(9, o.shape[0])
+    ref = oracle.trace(tree, o, k, emit=True)
+    g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 0.8)
+    g, n = _launches(hg, lambda: hg.tau_gradient(grid, _cuda(o), _cuda(k), _cuda(w, torch.float32), kappa=0.8,
+                                                 grad_precision="fp64", split="force"))
+    assert n == 5
+    np.testing.assert_allclose(_np(g), g_ref, rtol=1e-12, atol=1e-300)
+
+
+def test_step_limit_turns_splitting_off(hg, disk_grids):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[0]
+    _, n = _launches(hg, lambda: hg.trace_rays(grid, _cuda(o), _cuda(k), split="force", max_steps=7))
+    assert n == 3
+
+
 def test_taufn_autograd_and_finite_differences(hg, disk_grids):
     model, grids, o, k = disk_grids
     grid, tree, H = grids[1]
@@ -299,7 +382,8 @@ def test_batch_matches_single_grid_launches(hg):
         tau, nc, st = b.trace(O, K, kappa=1.4, precision=prec)
         for i, g in enumerate(grids):
             s = slice(begins[i], begins[i + 1])
-            t1, n1, s1 = hg.trace_rays(g, O[s].contiguous(), K[s].contiguous(), kappa=1.4, precision=prec)
+            t1, n1, s1 = hg.trace_rays(g, O[s].contiguous(), K[s].contiguous(), kappa=1.4, precision=prec,
+                                       split="off")
             np.testing.assert_array_equal(_np(tau[s]), _np(t1))
             np.testing.assert_array_equal(_np(nc[s]), _np(n1))
             np.testing.assert_array_equal(_np(st[s]), _np(s1))
@@ -343,11 +427,13 @@ def test_autotune_keeps_results(hg, disk_grids):
     model, grids, o, k = disk_grids
     grid, tree, _ = grids[1]
     O, K = _cuda(o), _cuda(k)
-    before = _np(hg.trace_rays(grid, O, K)[0])
+    before = hg.trace_rays(grid, O, K)
     cfg, ms = hg.autotune(grid, O, K)
     assert cfg["block"] in (128, 256) and cfg["schedule"] in (1, 2, 3) and cfg["min_blocks"] in (3, 4) and ms > 0
-    after = _np(hg.trace_rays(grid, O, K)[0])
-    np.testing.assert_array_equal(before, after)
+    after = hg.trace_rays(grid, O, K)
+    # counts are exact; tau may differ in the grouping of additions when the tuned schedule splits paths
+    np.testing.assert_array_equal(_np(before[1]), _np(after[1]))
+    _check_tau(_np(after[0]), _np(before[0]), 1e-13)
 
 
 # ----------------------------------------------------------------------------- full-size disk grids
