@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) batch_setup_kernel(const BatchArgs A) {
 // Rays of the whole batch: queue positions from a warp-aggregated atomic
 // counter, mapped to (grid, ray) through the queue offsets in shared memory.
 struct BatchRays {
+    static constexpr bool kSegments = false;
     const BatchArgs *A;
     const int64_t *s_qbeg;
     const int32_t *s_perm;

@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(256) order_kernel(int64_t n, const float *__re
 // Rays of one grid for the walking loop: a static stride, or a
 // warp-aggregated atomic on a global counter.
 struct GridRays {
+    static constexpr bool kSegments = true;
     const DevGrid *G;
     int64_t n;
     int64_t cursor;

@@ -381,6 +381,7 @@ __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned c
 // Take a ray for walking from its start record.  Returns WALK_GO with S
 // filled (S.cur = first leaf, not loaded yet), or WALK_END with the setup
 // status in *st.
+template <bool SEGS>
 __device__ __forceinline__ int ray_resume(const double *__restrict__ o, const double *__restrict__ d,
                                           const double *__restrict__ smax, const RayStart *__restrict__ starts,
                                           int64_t r, RayState &S, uint32_t *st) {
@@ -390,7 +391,7 @@ __device__ __forceinline__ int ray_resume(const double *__restrict__ o, const do
     // c = {cur, sg | status << 8, pad, pad}
     *st = (uint32_t)c.y >> 8;
     if (c.x < 0) return WALK_END;
-    if ((uint32_t)c.y & SG_SPLIT) return WALK_SKIP;  // its segments do the work
+    if (SEGS && ((uint32_t)c.y & SG_SPLIT)) return WALK_SKIP;  // its segments do the work
     S.ik0 = a.x;
     S.ik1 = a.y;
     S.ik2 = b.x;
@@ -405,7 +406,7 @@ __device__ __forceinline__ int ray_resume(const double *__restrict__ o, const do
     S.k1 = d[3 * r + 1];
     S.k2 = d[3 * r + 2];
     S.ktend = smax ? okey(smax[r]) : KEY_INF;
-    S.ktstop = KEY_INF;
+    if (SEGS) S.ktstop = KEY_INF;
     S.steps = 0;
     return WALK_GO;
 }
@@ -455,6 +456,7 @@ __device__ __forceinline__ long long wall_time(bool pos, bool neg, long long lo,
 // the path ends inside the leaf).  Returns WALK_END when the walk stops
 // after this leaf's segment (the path ends, leaves the domain, or a path
 // segment reaches its stop time), WALK_GO when the next leaf follows.
+template <bool SEGS>
 __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Leaf &L, double *ds, bool *rec,
                                         int *ax_out, double *tex_out, uint32_t *st) {
     *ds = 0.0;
@@ -483,7 +485,7 @@ __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Le
     S.ktcur = kt;
     *ax_out = ax;
     *tex_out = tex;
-    if (ax < 0 || kt > S.ktstop) return WALK_END;
+    if (ax < 0 || (SEGS && kt > S.ktstop)) return WALK_END;
     if (L.first(2 * ax + (dpos(sg, ax) ? 1 : 0)) < 0) return WALK_END;  // exit wall on the domain boundary
     return WALK_GO;
 }
@@ -618,11 +620,13 @@ struct WalkIO {
 // search found -- so a lane that missed the list head costs its warp one
 // more iteration instead of a chain of dependent loads inside one.
 // Src hands out rays: bool next(int64_t &ray, const DevGrid *&G, int32_t &max_steps);
-// an item ray >= io.n_rays is path segment ray - io.n_rays of a split ray.
+// when Src::kSegments, an item ray >= io.n_rays is path segment
+// ray - io.n_rays of a split ray (otherwise that code is compiled out).
 //   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
 //   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
 template <int KIND, int MODE, int PREC, class Src>
 __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem) {
+    constexpr bool SEGS = Src::kSegments;
     const DevGrid *Gp = nullptr;
     int64_t ray = 0;
     int32_t max_steps = 0;
@@ -649,10 +653,10 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             int64_t r = ray;
             int rs = WALK_GO;
             st = 0;
-            if (ray >= io.n_rays)
+            if (SEGS && ray >= io.n_rays)
                 rs = seg_resume(io.o, io.d, io.smax, io.starts, io.segs, ray - io.n_rays, S, &r);
             else
-                rs = ray_resume(io.o, io.d, io.smax, io.starts, ray, S, &st);
+                rs = ray_resume<SEGS>(io.o, io.d, io.smax, io.starts, ray, S, &st);
             if (rs == WALK_SKIP) {
                 have = false;
                 continue;
@@ -688,9 +692,9 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             double ds, tex;
             bool rec;
             int ax;
-            const int r = ray_exit(max_steps, S, L, &ds, &rec, &ax, &tex, &st);
-            const bool skip = (S.sg & SG_SKIP_FIRST) != 0;  // the segment before records this leaf
-            S.sg &= ~SG_SKIP_FIRST;
+            const int r = ray_exit<SEGS>(max_steps, S, L, &ds, &rec, &ax, &tex, &st);
+            const bool skip = SEGS && (S.sg & SG_SKIP_FIRST) != 0;  // the segment before records this leaf
+            if (SEGS) S.sg &= ~SG_SKIP_FIRST;
             if (rec && !skip) {
                 if (MODE == MODE_TAU) {
                     if (PREC == HG_FP64) {
@@ -730,7 +734,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             }
         }
     finish:
-        if (ray >= io.n_rays) {
+        if (SEGS && ray >= io.n_rays) {
             const int64_t sidx = ray - io.n_rays;
             if (MODE == MODE_TAU) {
                 io.part_acc[sidx] = (PREC == HG_FP64) ? acc : (double)acc32;
