@@ -283,6 +283,39 @@ hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *o, const do
                           double kappa, const float *w, int32_t grad_precision, void *grad_rho,
                           const hg_trace_opts *opts, hg_stream stream);
 
+/* ------------------------------------------------------------------------ prepared rays
+ * The optical-depth, emission and adjoint walks of one ray batch (Sect. 2.3
+ * for each) share their setup: 1/d, clip, first leaf, the work-ordered queue
+ * and the path segments.  hg_rays_prepare does that once; the walks below
+ * then reuse it.  The rays' arrays (o, d, s_max) are read by every walk and
+ * must stay unchanged until hg_rays_free.  Launch options (block,
+ * smem_nodes, schedule, min_blocks, split, max_steps) are fixed at
+ * preparation; the precision of each walk is given per call.  With path
+ * segments (see hg_trace_opts.split), hg_rays_fill writes each segment's
+ * cells after the crossings of the ray's earlier segments, which the last
+ * hg_rays_trace on the same rays counted, so a fill needs a trace first
+ * (HG_EINVAL otherwise); results are those of the one-shot calls. */
+typedef struct hg_rays hg_rays;
+
+/* Prepare n rays (o, d dev f64[n][3]; s_max dev f64[n] or NULL) on grid g.
+ * *out receives a handle owning device scratch (stream-ordered on stream). */
+hg_status hg_rays_prepare(const hg_grid *g, int64_t n, const double *o, const double *d, const double *s_max,
+                          const hg_trace_opts *opts, hg_rays **out, hg_stream stream);
+/* As hg_trace_rays (rho: dev f64[n_leaves] replacing the grid's densities,
+ * or NULL).  Records the segments' crossing counts for hg_rays_fill. */
+hg_status hg_rays_trace(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
+                        int32_t *ncross, uint8_t *ray_status, hg_stream stream);
+/* As hg_trace_fill; seg_off from hg_scan_offsets over the ncross of
+ * hg_rays_trace on the same rays. */
+hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
+                       int64_t seg_capacity, uint8_t *ray_status, hg_stream stream);
+/* As hg_tau_gradient (grad_rho ACCUMULATED). */
+hg_status hg_rays_gradient(hg_rays *r, double kappa, const float *w, int32_t grad_precision, void *grad_rho,
+                           hg_stream stream);
+/* Release the handle; its scratch is freed in order on stream (the stream of
+ * its last walk).  NULL is ignored. */
+void hg_rays_free(hg_rays *r, hg_stream stream);
+
 /* OR of the per-ray status bits into *out_bits (dev u32, overwritten). */
 hg_status hg_reduce_status(int64_t n, const uint8_t *ray_status, uint32_t *out_bits, hg_stream stream);
 /* Map OR-ed ray bits to one call-level status (host). */

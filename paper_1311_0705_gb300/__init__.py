@@ -107,6 +107,11 @@ _SIGS = {
     "hg_trace_fill": (_S, [_V, _I64, _V, _V, _V, C.POINTER(TraceOpts), _V, _V, _V, _I64, _V, _V]),
     "hg_sample_density": (_S, [_V, _I64, _V, _V, _V, _V]),
     "hg_tau_gradient": (_S, [_V, _I64, _V, _V, _V, C.c_double, _V, C.c_int32, _V, C.POINTER(TraceOpts), _V]),
+    "hg_rays_prepare": (_S, [_V, _I64, _V, _V, _V, C.POINTER(TraceOpts), C.POINTER(_V), _V]),
+    "hg_rays_trace": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V]),
+    "hg_rays_fill": (_S, [_V, C.c_int32, _V, _V, _V, _I64, _V, _V]),
+    "hg_rays_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V]),
+    "hg_rays_free": (None, [_V, _V]),
     "hg_reduce_status": (_S, [_I64, _V, _V, _V]),
     "hg_status_from_bits": (_S, [C.c_uint32]),
     "hg_load_model": (_S, [C.POINTER(_Model), C.POINTER(_V)]),
@@ -478,6 +483,92 @@ def tau_gradient(grid: Grid, o, d, w, s_max=None, kappa: float = 1.0, grad=None,
                                 _dptr(grad, gdt, (grid.n_leaves,), "grad"), C.byref(op), _stream()),
            "hg_tau_gradient")
     return grad
+
+
+class Rays:
+    """Prepared rays (hg_rays_prepare): one setup -- 1/d, clip, first leaf, work-ordered queue and
+    path segments -- shared by the optical-depth, emission and adjoint walks of the same rays.
+    The tensors o, d (and s_max) are kept referenced and must not change while the object lives."""
+
+    def __init__(self, grid: Grid, o, d, s_max=None, **opt):
+        n, po, pd, ps = _rays(o, d, s_max)
+        self.grid, self.n, self._keep = grid, n, (o, d, s_max)
+        self.device = o.device
+        op = _opts("fp64", **opt)
+        h = C.c_void_p()
+        _check(_lib.hg_rays_prepare(grid.handle, n, po, pd, ps, C.byref(op), C.byref(h), _stream()),
+               "hg_rays_prepare")
+        self._h = h
+
+    def trace(self, kappa: float = 1.0, precision="fp64", rho=None, out=None, status: bool = True):
+        """tau, ncross, status (hg_rays_trace)."""
+        torch = _torch()
+        n = self.n
+        prec = {"fp64": FP64, "fp32k": FP32K}[precision]
+        tdt = torch.float64 if prec == FP64 else torch.float32
+        if out is None:
+            tau = torch.empty(n, dtype=tdt, device=self.device)
+            nc = torch.empty(n, dtype=torch.int32, device=self.device)
+            st = torch.empty(n, dtype=torch.uint8, device=self.device) if status else None
+        else:
+            tau, nc, st = out
+        pr = None if rho is None else _dptr(rho, torch.float64, (self.grid.n_leaves,), "rho")
+        _check(_lib.hg_rays_trace(self._h, float(kappa), pr, prec, _dptr(tau, tdt, (n,), "tau"),
+                                  _dptr(nc, torch.int32, (n,), "ncross"), _dptr(st, torch.uint8, (n,), "status"),
+                                  _stream()), "hg_rays_trace")
+        return tau, nc, st
+
+    def fill(self, seg_off, precision="fp64", capacity: Optional[int] = None, status=None, out=None):
+        """Emitted cells and lengths (hg_rays_fill) at the offsets of a trace of these rays."""
+        torch = _torch()
+        n = self.n
+        prec = {"fp64": FP64, "fp32k": FP32K}[precision]
+        ddt = torch.float64 if prec == FP64 else torch.float32
+        if capacity is None:
+            capacity = int(seg_off[-1].item())
+        if out is None:
+            cell = torch.empty(max(capacity, 1), dtype=torch.int32, device=self.device)
+            ds = torch.empty(max(capacity, 1), dtype=ddt, device=self.device)
+        else:
+            cell, ds = out
+        _check(_lib.hg_rays_fill(self._h, prec, _dptr(seg_off, torch.int64, (n + 1,)), _dptr(cell),
+                                 _dptr(ds, ddt), int(capacity), _dptr(status, torch.uint8, (n,), "status"),
+                                 _stream()), "hg_rays_fill")
+        return cell[:capacity], ds[:capacity]
+
+    def emit(self, kappa: float = 1.0, precision="fp64"):
+        """Counting pass + scan + emission on these rays: tau, ncross, status, seg_off, seg_cell, seg_ds."""
+        tau, nc, st = self.trace(kappa, precision)
+        off = scan_offsets(nc)
+        cell, ds = self.fill(off, precision, status=st)
+        return dict(tau=tau, ncross=nc, status=st, seg_off=off, seg_cell=cell, seg_ds=ds)
+
+    def gradient(self, w, kappa: float = 1.0, grad=None, grad_precision="fp32"):
+        """Accumulate d(sum_r w_r tau_r)/d(rho) into ``grad`` (hg_rays_gradient); returns grad."""
+        torch = _torch()
+        gp = {"fp64": 0, "fp32": 1}[grad_precision]
+        gdt = torch.float64 if gp == 0 else torch.float32
+        if grad is None:
+            grad = torch.zeros(self.grid.n_leaves, dtype=gdt, device=self.device)
+        _check(_lib.hg_rays_gradient(self._h, float(kappa), _dptr(w, torch.float32, (self.n,), "w"), gp,
+                                     _dptr(grad, gdt, (self.grid.n_leaves,), "grad"), _stream()),
+               "hg_rays_gradient")
+        return grad
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.hg_rays_free(self._h, _stream())
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def prepare_rays(grid: Grid, o, d, s_max=None, **opt) -> Rays:
+    return Rays(grid, o, d, s_max, **opt)
 
 
 def reduce_status(status):

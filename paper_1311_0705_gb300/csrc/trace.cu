@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <new>
 
 #include "hg_internal.h"
 #include "walk.cuh"
@@ -45,6 +46,7 @@ struct TraceArgs {
     int32_t *part_nc;
     int32_t *part_last;
     uint8_t *part_st;
+    const int64_t *seg_base;  // emission offset of each path segment (fill walks)
 };
 
 // Stage the first n nodes of the (breadth-first) node list in shared memory.
@@ -290,6 +292,24 @@ __global__ void __launch_bounds__(256) split_kernel(const DevGrid G, int64_t n, 
     }
 }
 
+// Where each path segment writes its emitted cells: after the crossings of
+// the ray's earlier segments (their counts from an optical-depth walk over
+// the same plan).
+__global__ void __launch_bounds__(256) seg_base_kernel(const SplitRec *__restrict__ list,
+                                                       const unsigned long long *split_count,
+                                                       const int64_t *__restrict__ seg_off,
+                                                       const int32_t *__restrict__ part_nc, int64_t *seg_base) {
+    const int64_t m = (int64_t)*split_count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const SplitRec rec = list[i];
+        int64_t b = seg_off[rec.ray];
+        for (int j = 0; j < rec.count; j++) {
+            seg_base[rec.first + j] = b;
+            b += part_nc[rec.first + j];
+        }
+    }
+}
+
 // Results of the split rays from their segments' partial results.
 template <int MODE, int PREC>
 __global__ void __launch_bounds__(256) combine_kernel(const SplitRec *__restrict__ list,
@@ -322,7 +342,11 @@ __global__ void __launch_bounds__(256) combine_kernel(const SplitRec *__restrict
                 static_cast<float *>(tau)[rec.ray] = (float)acc;
             ncross[rec.ray] = nc;
         }
-        if (status) status[rec.ray] = (uint8_t)st;
+        if (MODE == MODE_FILL) {
+            if (status && st) status[rec.ray] |= (uint8_t)st;
+        } else if (status) {
+            status[rec.ray] = (uint8_t)st;
+        }
     }
 }
 
@@ -444,6 +468,7 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.part_nc = A.part_nc;
     io.part_last = A.part_last;
     io.part_st = A.part_st;
+    io.seg_base = A.seg_base;
     walk_loop<KIND, MODE, PREC>(src, io, smem, A.n_smem);
 }
 
@@ -517,12 +542,7 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
     return HG_OK;
 }
 
-hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int block, int smem_nodes, int schedule,
-                       int min_blocks, int split, cudaStream_t stream) {
-    if (A.n == 0) return HG_OK;
-    KernelFn k = pick_kernel(g->d.kind, mode, prec, min_blocks);
-    const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
-    const size_t smem = (size_t)smem_nodes * node_bytes;
+void set_smem_limits() {
     static std::once_flag once;
     std::call_once(once, [] {
         for (int kd = 0; kd < 2; kd++)
@@ -536,6 +556,10 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
         cudaFuncSetAttribute(split_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(split_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
+}
+
+// Resident blocks of a walking kernel for a launch shape.
+hg_status walk_blocks(KernelFn k, int block, size_t smem, int64_t n, int64_t &blocks) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
     if (e != cudaSuccess) return cuda_err(e, "occupancy query");
@@ -543,140 +567,230 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
         set_error("launch shape does not fit on an SM (block %d, %zu B shared)", block, smem);
         return HG_EINVAL;
     }
-    int64_t blocks = (int64_t)per_sm * sm_count();
-    const int64_t need = (A.n + block - 1) / block;
-    if (blocks > need) blocks = need;
-    const int64_t threads = blocks * block;
+    blocks = std::min<int64_t>((int64_t)per_sm * sm_count(), (n + block - 1) / block);
+    return HG_OK;
+}
+
+}  // namespace hg
+
+// Setup, queue order and path segments of one ray batch on one grid: what
+// every walk over these rays shares.  Owns one stream-ordered scratch
+// allocation.
+struct hg_rays {
+    const hg_grid *g = nullptr;
+    int64_t n = 0;
+    const double *o = nullptr, *d = nullptr, *smax = nullptr;
+    int block = 256, smem_nodes = 0, min_blocks = 3;
+    int64_t max_steps = 0, threads = 0;
+    bool dyn = false, ordered = false, splitting = false;
+    bool traced = false;  // an optical-depth walk recorded the segments' crossing counts
+    size_t smem = 0;
+    unsigned char *scratch = nullptr;
+    hg::RayStart *starts = nullptr;
+    int64_t *order = nullptr;
+    float *work = nullptr;
+    unsigned long long *counts = nullptr, *work_total = nullptr, *seg_count = nullptr, *split_count = nullptr,
+                       *queue = nullptr;
+    hg::SegStart *segs = nullptr;
+    double *part_acc = nullptr;
+    int32_t *part_nc = nullptr, *part_last = nullptr;
+    uint8_t *part_st = nullptr;
+    int64_t *seg_base = nullptr;
+    hg::SplitRec *list = nullptr;
+    int64_t seg_cap = 0;
+};
+
+namespace hg {
+
+// Build a plan: scratch, setup pass, and for the ordered schedule the
+// work-ordered queue and (when allowed) the path segments.
+//   exact: per-ray crossing offsets that order the queue exactly, or NULL.
+hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, const double *d, const double *smax,
+                    int block, int smem_nodes, int schedule, int min_blocks, int64_t max_steps, bool allow_split,
+                    int split, const int64_t *exact, cudaStream_t stream) {
+    set_smem_limits();
+    P.g = g;
+    P.n = n;
+    P.o = o;
+    P.d = d;
+    P.smax = smax;
+    P.block = block;
+    P.smem_nodes = smem_nodes;
+    P.min_blocks = min_blocks;
+    P.max_steps = max_steps;
+    const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
+    P.smem = (size_t)smem_nodes * node_bytes;
+    int64_t blocks = 0;
+    hg_status hs = walk_blocks(pick_kernel(g->d.kind, MODE_TAU, HG_FP64, min_blocks), block, P.smem, n, blocks);
+    if (hs != HG_OK) return hs;
+    P.threads = blocks * block;
     // auto schedule: order by estimated work only when each resident thread
     // gets few paths (then the heaviest paths would otherwise set the end)
-    if (schedule == 0) schedule = (A.n < 48 * threads) ? 3 : 2;
-    A.n_smem = smem_nodes;
-    A.dyn = (schedule >= 2);
-    const bool ordered = (schedule == 3);
-    // long paths are cut into segments in the modes whose per-ray results add up
-    const bool splitting = ordered && split != HG_SPLIT_OFF && (mode == MODE_TAU || mode == MODE_ADJ) && g->d.work;
-    const int64_t seg_cap =
-        splitting ? std::min<int64_t>((split == HG_SPLIT_FORCE ? 16 * A.n : 3 * threads) + 1024, 16 * A.n) : 0;
-    // scratch: start records; for the ordered schedule the queue and its
-    // counters (bucket counts and fills, work total, segment and split-ray
-    // counts); for splitting the segment records, partial results and the
-    // list of split rays
+    if (schedule == 0) schedule = (n < 48 * P.threads) ? 3 : 2;
+    P.dyn = (schedule >= 2);
+    P.ordered = (schedule == 3);
+    P.splitting = P.ordered && allow_split && split != HG_SPLIT_OFF && g->d.work;
+    P.seg_cap = P.splitting ? std::min<int64_t>((split == HG_SPLIT_FORCE ? 16 * n : 3 * P.threads) + 1024, 16 * n)
+                            : 0;
+    // scratch: start records; the queue counter; for the ordered schedule the
+    // queue, work estimates and counters (bucket counts and fills, work
+    // total, segment and split-ray counts); for splitting the segment
+    // records, partial results, emission offsets and the list of split rays
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t start_bytes = al((size_t)A.n * sizeof(RayStart));
-    const size_t order_bytes = ordered ? al((size_t)A.n * sizeof(int64_t)) : 0;
-    const size_t work_bytes = ordered ? al((size_t)A.n * sizeof(float)) : 0;
-    const size_t count_bytes = ordered ? al((2 * kBuckets + 3) * sizeof(unsigned long long)) : 0;
-    const size_t seg_bytes = al((size_t)seg_cap * sizeof(SegStart));
-    const size_t acc_bytes = al((size_t)seg_cap * sizeof(double));
-    const size_t i32_bytes = al((size_t)seg_cap * sizeof(int32_t));
-    const size_t u8_bytes = al((size_t)seg_cap);
-    const size_t list_bytes = al((size_t)(seg_cap / 2) * sizeof(SplitRec));
+    const size_t start_bytes = al((size_t)n * sizeof(RayStart));
+    const size_t order_bytes = P.ordered ? al((size_t)n * sizeof(int64_t)) : 0;
+    const size_t work_bytes = P.ordered ? al((size_t)n * sizeof(float)) : 0;
+    const size_t count_bytes = al((2 * kBuckets + 4) * sizeof(unsigned long long));
+    const size_t seg_bytes = al((size_t)P.seg_cap * sizeof(SegStart));
+    const size_t acc_bytes = al((size_t)P.seg_cap * sizeof(double));
+    const size_t i32_bytes = al((size_t)P.seg_cap * sizeof(int32_t));
+    const size_t u8_bytes = al((size_t)P.seg_cap);
+    const size_t base_bytes = al((size_t)P.seg_cap * sizeof(int64_t));
+    const size_t list_bytes = al((size_t)(P.seg_cap / 2) * sizeof(SplitRec));
     const size_t total_bytes = start_bytes + order_bytes + work_bytes + count_bytes + seg_bytes + acc_bytes +
-                               2 * i32_bytes + u8_bytes + list_bytes;
-    unsigned char *scratch = nullptr;
-    e = cudaMallocAsync((void **)&scratch, total_bytes, stream);
-    if (e != cudaSuccess) return cuda_err(e, "ray start scratch");
+                               2 * i32_bytes + u8_bytes + base_bytes + list_bytes;
+    cudaError_t e = cudaMallocAsync((void **)&P.scratch, total_bytes, stream);
+    if (e != cudaSuccess) {
+        P.scratch = nullptr;
+        return cuda_err(e, "ray plan scratch");
+    }
     size_t off = 0;
     auto take = [&](size_t b) {
-        unsigned char *p = b ? scratch + off : nullptr;
+        unsigned char *q = b ? P.scratch + off : nullptr;
         off += b;
-        return p;
+        return q;
     };
-    RayStart *starts = reinterpret_cast<RayStart *>(take(start_bytes));
-    int64_t *order = reinterpret_cast<int64_t *>(take(order_bytes));
-    float *work = reinterpret_cast<float *>(take(work_bytes));
-    unsigned long long *counts = reinterpret_cast<unsigned long long *>(take(count_bytes));
-    SegStart *segs = reinterpret_cast<SegStart *>(take(seg_bytes));
-    A.part_acc = reinterpret_cast<double *>(take(acc_bytes));
-    A.part_nc = reinterpret_cast<int32_t *>(take(i32_bytes));
-    A.part_last = reinterpret_cast<int32_t *>(take(i32_bytes));
-    A.part_st = reinterpret_cast<uint8_t *>(take(u8_bytes));
-    SplitRec *list = reinterpret_cast<SplitRec *>(take(list_bytes));
-    unsigned long long *work_total = counts ? counts + 2 * kBuckets : nullptr;
-    unsigned long long *seg_count = counts ? counts + 2 * kBuckets + 1 : nullptr;
-    unsigned long long *split_count = counts ? counts + 2 * kBuckets + 2 : nullptr;
-    if (counts) {
-        e = cudaMemsetAsync(counts, 0, count_bytes, stream);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(scratch, stream);
-            return cuda_err(e, "scratch reset");
-        }
-    }
-    const int64_t sblocks = std::min<int64_t>((A.n + 255) / 256, (int64_t)sm_count() * 8);
-    {
-        // the fill pass knows each ray's exact crossing count from its offsets
-        const int64_t *exact = (mode == MODE_FILL) ? A.seg_off : nullptr;
-        if (g->d.kind == HG_KDTREE)
-            setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
-                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, counts, exact, work_total, work);
-        else
-            setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
-                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, counts, exact, work_total, work);
+    P.starts = reinterpret_cast<RayStart *>(take(start_bytes));
+    P.order = reinterpret_cast<int64_t *>(take(order_bytes));
+    P.work = reinterpret_cast<float *>(take(work_bytes));
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(take(count_bytes));
+    P.segs = reinterpret_cast<SegStart *>(take(seg_bytes));
+    P.part_acc = reinterpret_cast<double *>(take(acc_bytes));
+    P.part_nc = reinterpret_cast<int32_t *>(take(i32_bytes));
+    P.part_last = reinterpret_cast<int32_t *>(take(i32_bytes));
+    P.part_st = reinterpret_cast<uint8_t *>(take(u8_bytes));
+    P.seg_base = reinterpret_cast<int64_t *>(take(base_bytes));
+    P.list = reinterpret_cast<SplitRec *>(take(list_bytes));
+    P.counts = P.ordered ? cnt : nullptr;
+    P.work_total = cnt + 2 * kBuckets;
+    P.seg_count = cnt + 2 * kBuckets + 1;
+    P.split_count = cnt + 2 * kBuckets + 2;
+    P.queue = cnt + 2 * kBuckets + 3;
+    e = cudaMemsetAsync(cnt, 0, count_bytes, stream);
+    if (e != cudaSuccess) return cuda_err(e, "scratch reset");
+    const int64_t sblocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    if (g->d.kind == HG_KDTREE)
+        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+            g->d, n, o, d, smax, P.starts, smem_nodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
+    else
+        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+            g->d, n, o, d, smax, P.starts, smem_nodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
+    note_launches(1);
+    if (P.ordered) {
+        order_kernel<<<(unsigned)sblocks, 256, 0, stream>>>(n, P.work, P.counts, P.counts + kBuckets, P.order);
         note_launches(1);
-        if (order) {
-            order_kernel<<<(unsigned)sblocks, 256, 0, stream>>>(A.n, work, counts, counts + kBuckets, order);
-            note_launches(1);
-        }
     }
-    if (splitting) {
+    if (P.splitting) {
         const int force = split == HG_SPLIT_FORCE ? 1 : 0;
         if (g->d.kind == HG_KDTREE)
-            split_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
-                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, work_total, counts, order, threads, force, segs,
-                seg_cap, seg_count, list, split_count);
+            split_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+                g->d, n, o, d, smax, P.starts, smem_nodes, P.work_total, P.counts, P.order, P.threads, force, P.segs,
+                P.seg_cap, P.seg_count, P.list, P.split_count);
         else
-            split_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(
-                g->d, A.n, A.o, A.d, A.smax, starts, smem_nodes, work_total, counts, order, threads, force, segs,
-                seg_cap, seg_count, list, split_count);
+            split_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+                g->d, n, o, d, smax, P.starts, smem_nodes, P.work_total, P.counts, P.order, P.threads, force, P.segs,
+                P.seg_cap, P.seg_count, P.list, P.split_count);
         note_launches(1);
-        A.n_seg = seg_count;
-        A.n_seg_cap = seg_cap;
-        A.segs = segs;
     }
-    A.starts = starts;
-    A.order = order;
-    unsigned long long *ctr = nullptr;
-    if (A.dyn) {
-        e = cudaMallocAsync((void **)&ctr, sizeof(unsigned long long), stream);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(scratch, stream);
-            return cuda_err(e, "scratch counter");
-        }
-        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(ctr, stream);
-            cudaFreeAsync(scratch, stream);
-            return cuda_err(e, "scratch counter");
-        }
-        A.counter = ctr;
-    }
-    k<<<(unsigned)blocks, block, smem, stream>>>(A);
     e = cudaGetLastError();
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "ray plan");
+}
+
+void free_plan(hg_rays &P, cudaStream_t stream) {
+    if (P.scratch) cudaFreeAsync(P.scratch, stream);
+    P.scratch = nullptr;
+}
+
+// One walk over a plan.  A carries the outputs of the mode (and kappa, w,
+// rho_ext); the plan supplies rays, start records, queue and segments.
+hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t stream) {
+    if (P.n == 0) return HG_OK;
+    const hg_grid *g = P.g;
+    KernelFn k = pick_kernel(g->d.kind, mode, prec, P.min_blocks);
+    int64_t blocks = 0;
+    hg_status hs = walk_blocks(k, P.block, P.smem, P.n, blocks);
+    if (hs != HG_OK) return hs;
+    A.G = g->d;
+    A.n = P.n;
+    A.o = P.o;
+    A.d = P.d;
+    A.smax = P.smax;
+    A.max_steps = P.max_steps;
+    A.n_smem = P.smem_nodes;
+    A.dyn = P.dyn ? 1 : 0;
+    A.starts = P.starts;
+    A.order = P.order;
+    A.counter = P.queue;
+    if (P.splitting) {
+        A.n_seg = P.seg_count;
+        A.n_seg_cap = P.seg_cap;
+        A.segs = P.segs;
+        A.part_acc = P.part_acc;
+        A.part_nc = P.part_nc;
+        A.part_last = P.part_last;
+        A.part_st = P.part_st;
+        A.seg_base = P.seg_base;
+    }
+    cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_err(e, "queue reset");
+    const unsigned cblocks =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((P.seg_cap / 2 + 255) / 256, (int64_t)sm_count() * 4));
+    if (P.splitting && mode == MODE_FILL) {
+        seg_base_kernel<<<cblocks, 256, 0, stream>>>(P.list, P.split_count, A.seg_off, P.part_nc, P.seg_base);
+        note_launches(1);
+    }
+    k<<<(unsigned)blocks, P.block, P.smem, stream>>>(A);
     note_launches(1);
-    if (e == cudaSuccess && splitting) {
-        const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((seg_cap / 2 + 255) / 256,
-                                                                                 (int64_t)sm_count() * 4));
+    e = cudaGetLastError();
+    if (e == cudaSuccess && P.splitting) {
         if (mode == MODE_TAU) {
             if (prec == HG_FP64)
                 combine_kernel<MODE_TAU, HG_FP64><<<cblocks, 256, 0, stream>>>(
-                    list, split_count, segs, A.part_acc, A.part_nc, A.part_last, A.part_st, A.kappa, A.tau, A.ncross,
-                    A.status);
+                    P.list, P.split_count, P.segs, P.part_acc, P.part_nc, P.part_last, P.part_st, A.kappa, A.tau,
+                    A.ncross, A.status);
             else
                 combine_kernel<MODE_TAU, HG_FP32K><<<cblocks, 256, 0, stream>>>(
-                    list, split_count, segs, A.part_acc, A.part_nc, A.part_last, A.part_st, A.kappa, A.tau, A.ncross,
-                    A.status);
+                    P.list, P.split_count, P.segs, P.part_acc, P.part_nc, P.part_last, P.part_st, A.kappa, A.tau,
+                    A.ncross, A.status);
+        } else if (mode == MODE_FILL) {
+            combine_kernel<MODE_FILL, 0><<<cblocks, 256, 0, stream>>>(P.list, P.split_count, P.segs, P.part_acc,
+                                                                    P.part_nc, P.part_last, P.part_st, A.kappa,
+                                                                    nullptr, nullptr, A.status);
         } else {
-            combine_kernel<MODE_ADJ, 0><<<cblocks, 256, 0, stream>>>(list, split_count, segs, A.part_acc, A.part_nc,
-                                                                   A.part_last, A.part_st, A.kappa, nullptr,
-                                                                   nullptr, A.status);
+            combine_kernel<MODE_ADJ, 0><<<cblocks, 256, 0, stream>>>(P.list, P.split_count, P.segs, P.part_acc,
+                                                                   P.part_nc, P.part_last, P.part_st, A.kappa,
+                                                                   nullptr, nullptr, A.status);
         }
-        e = cudaGetLastError();
         note_launches(1);
+        e = cudaGetLastError();
     }
-    if (ctr) cudaFreeAsync(ctr, stream);
-    cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) return cuda_err(e, "trace launch");
+    if (mode == MODE_TAU) P.traced = true;
     return HG_OK;
+}
+
+// A one-shot walk: plan, walk, free.  Long paths are cut only in the modes
+// whose per-ray results add up (a one-shot fill has no segment counts).
+hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int block, int smem_nodes, int schedule,
+                       int min_blocks, int split, cudaStream_t stream) {
+    if (A.n == 0) return HG_OK;
+    hg_rays P;
+    hg_status hs = make_plan(P, g, A.n, A.o, A.d, A.smax, block, smem_nodes, schedule, min_blocks, A.max_steps,
+                             mode == MODE_TAU || mode == MODE_ADJ, split, mode == MODE_FILL ? A.seg_off : nullptr,
+                             stream);
+    if (hs == HG_OK) hs = walk_plan(P, mode, prec, A, stream);
+    free_plan(P, stream);
+    return hs;
 }
 
 hg_status check_rays(const hg_grid *g, int64_t n, const double *o, const double *d) {
@@ -924,6 +1038,118 @@ extern "C" hg_status hg_tau_gradient(const hg_grid *g, int64_t n, const double *
     A.max_steps = max_steps;
     return launch_trace(g, MODE_ADJ, grad_precision, A, block, smem_nodes, schedule, min_blocks, split,
                         (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ prepared rays
+
+extern "C" hg_status hg_rays_prepare(const hg_grid *g, int64_t n, const double *o, const double *d,
+                                     const double *s_max, const hg_trace_opts *opts, hg_rays **out,
+                                     hg_stream stream) {
+    if (!out) {
+        set_error("hg_rays_prepare: out is required");
+        return HG_EINVAL;
+    }
+    *out = nullptr;
+    hg_status st = check_rays(g, n, o, d);
+    if (st != HG_OK) return st;
+    int prec, block, smem_nodes, schedule, min_blocks, split;
+    int64_t max_steps;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps, split)) != HG_OK) return st;
+    hg_rays *r = new (std::nothrow) hg_rays;
+    if (!r) {
+        set_error("hg_rays_prepare: out of host memory");
+        return HG_ENOMEM;
+    }
+    if (n > 0) {
+        st = make_plan(*r, g, n, o, d, s_max, block, smem_nodes, schedule, min_blocks, max_steps, true, split, nullptr,
+                       (cudaStream_t)stream);
+        if (st != HG_OK) {
+            free_plan(*r, (cudaStream_t)stream);
+            delete r;
+            return st;
+        }
+    }
+    r->g = g;
+    r->n = n;
+    *out = r;
+    return HG_OK;
+}
+
+extern "C" hg_status hg_rays_trace(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
+                                   int32_t *ncross, uint8_t *ray_status, hg_stream stream) {
+    if (!r) {
+        set_error("hg_rays_trace: null rays");
+        return HG_EINVAL;
+    }
+    if (precision != HG_FP64 && precision != HG_FP32K) {
+        set_error("precision must be HG_FP64 or HG_FP32K");
+        return HG_EINVAL;
+    }
+    if (r->n > 0 && (!tau || !ncross)) {
+        set_error("hg_rays_trace: tau and ncross are required");
+        return HG_EINVAL;
+    }
+    TraceArgs A{};
+    A.kappa = kappa;
+    A.tau = tau;
+    A.ncross = ncross;
+    A.status = ray_status;
+    A.rho_ext = rho;
+    return walk_plan(*r, MODE_TAU, precision, A, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell,
+                                  void *seg_ds, int64_t seg_capacity, uint8_t *ray_status, hg_stream stream) {
+    if (!r) {
+        set_error("hg_rays_fill: null rays");
+        return HG_EINVAL;
+    }
+    if (precision != HG_FP64 && precision != HG_FP32K) {
+        set_error("precision must be HG_FP64 or HG_FP32K");
+        return HG_EINVAL;
+    }
+    if (r->n > 0 && (!seg_off || (seg_capacity > 0 && (!seg_cell || !seg_ds)) || seg_capacity < 0)) {
+        set_error("hg_rays_fill: bad segment arrays");
+        return HG_EINVAL;
+    }
+    if (r->splitting && !r->traced) {
+        set_error("hg_rays_fill: these rays are walked as path segments; call hg_rays_trace on them first");
+        return HG_EINVAL;
+    }
+    TraceArgs A{};
+    A.seg_off = seg_off;
+    A.seg_cell = seg_cell;
+    A.seg_ds = seg_ds;
+    A.seg_cap = seg_capacity;
+    A.status = ray_status;
+    return walk_plan(*r, MODE_FILL, precision, A, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_rays_gradient(hg_rays *r, double kappa, const float *w, int32_t grad_precision,
+                                      void *grad_rho, hg_stream stream) {
+    if (!r) {
+        set_error("hg_rays_gradient: null rays");
+        return HG_EINVAL;
+    }
+    if (r->n > 0 && (!w || !grad_rho)) {
+        set_error("hg_rays_gradient: w and grad_rho are required");
+        return HG_EINVAL;
+    }
+    if (grad_precision != 0 && grad_precision != 1) {
+        set_error("hg_rays_gradient: grad_precision must be 0 (f64) or 1 (f32)");
+        return HG_EINVAL;
+    }
+    TraceArgs A{};
+    A.kappa = kappa;
+    A.w = w;
+    A.grad = grad_rho;
+    return walk_plan(*r, MODE_ADJ, grad_precision, A, (cudaStream_t)stream);
+}
+
+extern "C" void hg_rays_free(hg_rays *r, hg_stream stream) {
+    if (!r) return;
+    free_plan(*r, (cudaStream_t)stream);
+    delete r;
 }
 
 extern "C" hg_status hg_sample_density(const hg_grid *g, int64_t n, const double *pts, int32_t *cell, double *rho,

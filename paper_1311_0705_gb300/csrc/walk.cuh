@@ -612,6 +612,7 @@ struct WalkIO {
     int32_t *part_nc = nullptr;    // partial crossing count
     int32_t *part_last = nullptr;  // leaf the segment stopped in
     uint8_t *part_st = nullptr;    // partial status bits
+    const int64_t *seg_base = nullptr;  // emission offset of each segment (MODE_FILL)
 };
 
 // The walking loop of one thread.  Each iteration loads exactly one leaf
@@ -661,7 +662,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                 have = false;
                 continue;
             }
-            if (MODE == MODE_FILL) seg_base = io.seg_off[r];
+            if (MODE == MODE_FILL) seg_base = (SEGS && ray >= io.n_rays) ? io.seg_base[ray - io.n_rays] : io.seg_off[r];
             if (MODE == MODE_ADJ) wk = io.kappa * (double)io.w[r];
             if (rs == WALK_END) goto finish;
             C.id = S.cur;

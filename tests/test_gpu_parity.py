@@ -329,6 +329,71 @@ def test_forced_segments_adjoint(hg, disk_grids, kind):
     np.testing.assert_allclose(_np(g), g_ref, rtol=1e-12, atol=1e-300)
 
 
+def _same_emission(out, ref, precision):
+    np.testing.assert_array_equal(_np(out["ncross"]), ref["ncross"])
+    np.testing.assert_array_equal(_np(out["status"]), ref["status"])
+    np.testing.assert_array_equal(_np(out["seg_off"]), ref["seg_off"])
+    np.testing.assert_array_equal(_np(out["seg_cell"]), ref["seg_cell"])
+    if precision == "fp64":
+        np.testing.assert_array_equal(_np(out["seg_ds"]), ref["seg_ds"])
+        _check_tau(_np(out["tau"]), ref["tau"], TAU_RTOL_FP64)
+    else:
+        np.testing.assert_array_equal(_np(out["seg_ds"]), ref["seg_ds"].astype(np.float32))
+        _check_tau(_np(out["tau"]), ref["tau"], TAU_RTOL_FP32K)
+
+
+@pytest.mark.parametrize("split", ["force", "auto", "off"])
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_prepared_rays_emission_bit_exact(hg, disk_grids, kind, split):
+    # segments emit their cells at offsets from the segment counts of the trace: the whole
+    # sequences and lengths must come out bit for bit as the oracle's
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    ref = oracle.trace(tree, o, k, kappa=0.7, emit=True)
+    R, n = _launches(hg, lambda: hg.prepare_rays(grid, _cuda(o), _cuda(k), split=split, schedule=3))
+    assert n == (2 if split == "off" else 3)  # setup, queue order (, split planner)
+    for prec in ("fp64", "fp32k"):
+        _same_emission(R.emit(kappa=0.7, precision=prec), ref, prec)
+    R.free()
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_prepared_rays_path_ends_and_gradient(hg, disk_grids, kind):
+    model, grids, _, _ = disk_grids
+    grid, tree, _ = grids[kind]
+    a, k, L = synth.endpoint_paths(79, 4001)
+    smax = 0.8 * L
+    ref = oracle.trace(tree, a, k, smax=smax, kappa=1.9, emit=True)
+    R = hg.prepare_rays(grid, _cuda(a), _cuda(k), _cuda(smax), split="force")
+    _same_emission(R.emit(kappa=1.9), ref, "fp64")
+    w = synth.adjoint_weights(13, a.shape[0])
+    g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 1.9)
+    g, n = _launches(hg, lambda: R.gradient(_cuda(w, torch.float32), kappa=1.9, grad_precision="fp64"))
+    assert n == 2  # walk, combine
+    np.testing.assert_allclose(_np(g), g_ref, rtol=1e-12, atol=1e-300)
+    # a second trace with other densities reuses the plan
+    rho = torch.full((tree.n_leaves,), 2.0, dtype=torch.float64, device="cuda")
+    tau2, nc2, _ = R.trace(kappa=1.0, rho=rho)
+    np.testing.assert_array_equal(_np(nc2), ref["ncross"])
+    seg_len = np.add.reduceat(ref["seg_ds"], ref["seg_off"][:-1][ref["ncross"] > 0]) if ref["seg_ds"].size else []
+    got = _np(tau2)[ref["ncross"] > 0]
+    np.testing.assert_allclose(got, 2.0 * np.asarray(seg_len), rtol=1e-12)
+
+
+def test_prepared_fill_needs_a_trace_when_paths_are_split(hg, disk_grids):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[0]
+    R = hg.prepare_rays(grid, _cuda(o), _cuda(k), split="force")
+    off = torch.zeros(o.shape[0] + 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(hg.HgError, match="hg_rays_trace"):
+        R.fill(off, capacity=0)
+    R.free()
+    R2 = hg.prepare_rays(grid, _cuda(o[:0]), _cuda(k[:0]))
+    tau, nc, st = R2.trace()
+    assert tau.numel() == 0
+    R2.free()
+
+
 def test_step_limit_turns_splitting_off(hg, disk_grids):
     model, grids, o, k = disk_grids
     grid, tree, _ = grids[0]
