@@ -47,6 +47,9 @@ UNIT = "rays/s"
 # wall's CSR range (2 x int64) + one neighbor id; per ray origin + direction in, tau + count + status out
 BYTES_PER_CROSSING = {"fp64": 48 + 8 + 16 + 4, "fp32k": 48 + 4 + 16 + 4}
 BYTES_PER_RAY = {"fp64": 48 + 8 + 4 + 1, "fp32k": 48 + 4 + 4 + 1}
+# the adjoint scatter fused into the same walk: an FP32 gradient read-modify-write per crossing, w per ray
+ADJ_BYTES_PER_CROSSING = 4 + 4
+ADJ_BYTES_PER_RAY = 4
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -267,9 +270,12 @@ def run_ours(args):
             if record:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            # one setup (first leaf, work-ordered queue, path segments) for the three walks of these rays
+            # one setup (first leaf, work-ordered queue, path segments) for the walks of these rays:
+            # optical depth, counts and the adjoint in one walk, then the emission fill
             R = hg.prepare_rays(G, O, K)
-            R.trace(kappa=1.0, precision=prec, out=(g["tau"], g["nc"], g["st"]))
+            g["grad"].zero_()
+            R.trace_gradient(W, kappa=1.0, precision=prec, grad=g["grad"], grad_precision="fp32",
+                             out=(g["tau"], g["nc"], g["st"]))
             if record:
                 e1.record(stream)
                 kev.append((g["name"], e0, e1))
@@ -283,8 +289,6 @@ def run_ours(args):
             drho = hg.diff_stats(RT, rg)
             ptau, _, _ = hg.trace_rays(G, PA, PK, PL, kappa=1.0, precision="fp64", out=(g["ptau"], g["pnc"], None))
             dtau = hg.diff_stats(TT, ptau)
-            g["grad"].zero_()
-            R.gradient(W, kappa=1.0, grad=g["grad"], grad_precision="fp32")
             R.free()
             out[g["name"]] = (ncs, drho, dtau)
         return out
@@ -332,7 +336,8 @@ def run_ours(args):
     for g in grids:
         cr = int(g["nc"].sum().item())
         ms = statistics.mean(per[g["name"]])
-        byt = BYTES_PER_CROSSING[prec] * cr + BYTES_PER_RAY[prec] * n_rays
+        byt = ((BYTES_PER_CROSSING[prec] + ADJ_BYTES_PER_CROSSING) * cr +
+               (BYTES_PER_RAY[prec] + ADJ_BYTES_PER_RAY) * n_rays)
         kern[g["name"]] = dict(leaves=g["grid"].n_leaves, build_s=round(g["build_s"], 2), load_s=round(g["load_s"], 2),
                                mean_ncross=cr / n_rays, trace_ms=ms, trace_rays_per_s=n_rays / ms * 1e3,
                                gcross_per_s=cr / ms / 1e6, algorithmic_bytes=byt,
@@ -349,8 +354,8 @@ def run_ours(args):
     achieved = tot_bytes / (tot_time / 1e3) / 1e9
     traffic = recorded_traffic(args.workload, prec)
     roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s", frac=round(achieved / peak, 4),
-                    traffic=traffic, kernel="trace_kernel, optical-depth walk incl. its setup "
-                                            "(hg_rays_prepare + hg_rays_trace)",
+                    traffic=traffic, kernel="trace_kernel, optical depth + adjoint walk incl. its setup "
+                                            "(hg_rays_prepare + hg_rays_trace_gradient)",
                     peak_source="measured" if "hbm_gbs" in peaks else "fallback")
 
     # e2e: the same step through the public API with host buffers (pinned), copies inside the timed region

@@ -305,8 +305,14 @@ hg_status hg_rays_prepare(const hg_grid *g, int64_t n, const double *o, const do
  * or NULL).  Records the segments' crossing counts for hg_rays_fill. */
 hg_status hg_rays_trace(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
                         int32_t *ncross, uint8_t *ray_status, hg_stream stream);
+/* hg_rays_trace and hg_rays_gradient in one walk: tau, ncross and status,
+ * and grad_rho += d(sum_r w_r tau_r)/d(rho) (ACCUMULATED), from the same
+ * segments. */
+hg_status hg_rays_trace_gradient(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
+                                 int32_t *ncross, uint8_t *ray_status, const float *w, int32_t grad_precision,
+                                 void *grad_rho, hg_stream stream);
 /* As hg_trace_fill; seg_off from hg_scan_offsets over the ncross of
- * hg_rays_trace on the same rays. */
+ * hg_rays_trace (or hg_rays_trace_gradient) on the same rays. */
 hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
                        int64_t seg_capacity, uint8_t *ray_status, hg_stream stream);
 /* As hg_tau_gradient (grad_rho ACCUMULATED). */

@@ -109,6 +109,7 @@ _SIGS = {
     "hg_tau_gradient": (_S, [_V, _I64, _V, _V, _V, C.c_double, _V, C.c_int32, _V, C.POINTER(TraceOpts), _V]),
     "hg_rays_prepare": (_S, [_V, _I64, _V, _V, _V, C.POINTER(TraceOpts), C.POINTER(_V), _V]),
     "hg_rays_trace": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V]),
+    "hg_rays_trace_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V, C.c_int32, _V, _V]),
     "hg_rays_fill": (_S, [_V, C.c_int32, _V, _V, _V, _I64, _V, _V]),
     "hg_rays_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V]),
     "hg_rays_free": (None, [_V, _V]),
@@ -517,6 +518,32 @@ class Rays:
                                   _dptr(nc, torch.int32, (n,), "ncross"), _dptr(st, torch.uint8, (n,), "status"),
                                   _stream()), "hg_rays_trace")
         return tau, nc, st
+
+    def trace_gradient(self, w, kappa: float = 1.0, precision="fp64", rho=None, grad=None, grad_precision="fp32",
+                       out=None, status: bool = True):
+        """tau, ncross, status and the accumulated gradient in one walk (hg_rays_trace_gradient)."""
+        torch = _torch()
+        n = self.n
+        prec = {"fp64": FP64, "fp32k": FP32K}[precision]
+        tdt = torch.float64 if prec == FP64 else torch.float32
+        gp = {"fp64": 0, "fp32": 1}[grad_precision]
+        gdt = torch.float64 if gp == 0 else torch.float32
+        if out is None:
+            tau = torch.empty(n, dtype=tdt, device=self.device)
+            nc = torch.empty(n, dtype=torch.int32, device=self.device)
+            st = torch.empty(n, dtype=torch.uint8, device=self.device) if status else None
+        else:
+            tau, nc, st = out
+        if grad is None:
+            grad = torch.zeros(self.grid.n_leaves, dtype=gdt, device=self.device)
+        pr = None if rho is None else _dptr(rho, torch.float64, (self.grid.n_leaves,), "rho")
+        _check(_lib.hg_rays_trace_gradient(self._h, float(kappa), pr, prec, _dptr(tau, tdt, (n,), "tau"),
+                                           _dptr(nc, torch.int32, (n,), "ncross"),
+                                           _dptr(st, torch.uint8, (n,), "status"),
+                                           _dptr(w, torch.float32, (n,), "w"), gp,
+                                           _dptr(grad, gdt, (self.grid.n_leaves,), "grad"), _stream()),
+               "hg_rays_trace_gradient")
+        return tau, nc, st, grad
 
     def fill(self, seg_off, precision="fp64", capacity: Optional[int] = None, status=None, out=None):
         """Emitted cells and lengths (hg_rays_fill) at the offsets of a trace of these rays."""

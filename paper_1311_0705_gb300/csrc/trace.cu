@@ -86,10 +86,15 @@ __global__ void __launch_bounds__(256) setup_kernel(const DevGrid G, int64_t n, 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int hist[kBuckets];
     if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
-    stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
+    const int node_bytes = n_smem * (KIND == HG_KDTREE ? 16 : 32);
+    // the work lattice follows the staged nodes when the pass estimates work
+    const bool estimate = bucket_count != nullptr && !seg_off;
+    float *lat = (estimate && G.work) ? reinterpret_cast<float *>(smem + node_bytes) : nullptr;
+    if (lat) stage_lattice(G, lat);
+    stage_nodes(G.nodes, node_bytes, smem);
     unsigned long long wsum = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        RayStart R = ray_setup<KIND>(G, smem, n_smem, o, d, smax, r, bucket_count != nullptr && !seg_off);
+        RayStart R = ray_setup<KIND>(G, smem, n_smem, o, d, smax, r, estimate, lat);
         if (seg_off) R.work = (float)(seg_off[r + 1] - seg_off[r]);
         starts[r] = R;
         if (work) work[r] = R.work;
@@ -163,12 +168,12 @@ __global__ void __launch_bounds__(256) split_kernel(const DevGrid G, int64_t n, 
                                                     const int64_t *__restrict__ order, int64_t threads, int force,
                                                     SegStart *segs, int64_t seg_cap, unsigned long long *seg_count,
                                                     SplitRec *list, unsigned long long *split_count) {
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t s_leaf[kPlanWarps][kMaxSegs];
     __shared__ long long s_key[kPlanWarps][kMaxSegs];
     __shared__ long long s_ncand;
-    stage_nodes(G.nodes, n_smem * (KIND == HG_KDTREE ? 16 : 32), smem);
+    __shared__ __align__(16) float lat[kWorkN * kWorkN * kWorkN];
     if (!G.work || G.work_n <= 0) return;
+    stage_lattice(G, lat);
     const float A = (float)*work_total / (float)threads;
     const float W = force ? 2.0f : fmaxf(32.0f, 0.5f * A);
     const float thr = force ? 3.0f : fmaxf(64.0f, A);
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(256) split_kernel(const DevGrid G, int64_t n, 
         const float target = R.work * (float)(lane + 1) / (float)K;
         float tc = 0.0f;
         bool found = false;
-        work_march(G, of, kf, ts, tend, [&](float t, float tn, float rate, float e) {
+        work_march(G, lat, of, kf, ts, tend, [&](float t, float tn, float rate, float e) {
             if (!found && rate > 0.0f && e + rate * (tn - t) >= target) {
                 tc = t + (target - e) / rate;
                 found = true;
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(256) split_kernel(const DevGrid G, int64_t n, 
             if (in_axis(q3[0], G.klo[0], G.khi[0], dpos(sg, 0), dneg(sg, 0), true) &&
                 in_axis(q3[1], G.klo[1], G.khi[1], dpos(sg, 1), dneg(sg, 1), true) &&
                 in_axis(q3[2], G.klo[2], G.khi[2], dpos(sg, 2), dneg(sg, 2), true))
-                Lid = descend<KIND>(G, smem, n_smem, q3[0], q3[1], q3[2], sg);
+                Lid = descend<KIND>(G, nullptr, 0, q3[0], q3[1], q3[2], sg);
             if (Lid >= 0) {
                 Leaf L;
                 load_leaf(G.rec, Lid, L);
@@ -476,11 +481,16 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
 
 typedef void (*KernelFn)(const TraceArgs);
 
+// Walking kernels by [kind][mode][prec][occupancy]; prec runs 0..1, and 0..3
+// for MODE_TAUADJ (optical depth and gradient precisions).
 KernelFn pick_kernel(int kind, int mode, int prec, int occ) {
 #define HG_K(K, M, P) {&trace_kernel<K, M, P, 3>, &trace_kernel<K, M, P, 4>}
-    static const KernelFn table[2][3][2][2] = {
-        {{HG_K(0, 0, 0), HG_K(0, 0, 1)}, {HG_K(0, 1, 0), HG_K(0, 1, 1)}, {HG_K(0, 2, 0), HG_K(0, 2, 1)}},
-        {{HG_K(1, 0, 0), HG_K(1, 0, 1)}, {HG_K(1, 1, 0), HG_K(1, 1, 1)}, {HG_K(1, 2, 0), HG_K(1, 2, 1)}}};
+#define HG_M(K, M) {HG_K(K, M, 0), HG_K(K, M, 1), {nullptr, nullptr}, {nullptr, nullptr}}
+#define HG_MA(K) {HG_K(K, 3, 0), HG_K(K, 3, 1), HG_K(K, 3, 2), HG_K(K, 3, 3)}
+    static const KernelFn table[2][4][4][2] = {{HG_M(0, 0), HG_M(0, 1), HG_M(0, 2), HG_MA(0)},
+                                                {HG_M(1, 0), HG_M(1, 1), HG_M(1, 2), HG_MA(1)}};
+#undef HG_MA
+#undef HG_M
 #undef HG_K
     return table[kind][mode][prec][occ == 4 ? 1 : 0];
 }
@@ -542,19 +552,21 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
     return HG_OK;
 }
 
+constexpr int kLatticeBytes = kWorkN * kWorkN * kWorkN * (int)sizeof(float);
+constexpr int kSetupSmemMax = 200 * 1024 + kLatticeBytes;
+
 void set_smem_limits() {
     static std::once_flag once;
     std::call_once(once, [] {
         for (int kd = 0; kd < 2; kd++)
-            for (int m = 0; m < 3; m++)
-                for (int p = 0; p < 2; p++)
+            for (int m = 0; m < 4; m++)
+                for (int p = 0; p < (m == MODE_TAUADJ ? 4 : 2); p++)
                     for (int oc = 3; oc <= 4; oc++)
                         cudaFuncSetAttribute(pick_kernel(kd, m, p, oc), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
-        cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(split_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(split_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        // the setup pass also stages the work lattice after the nodes
+        cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemMax);
+        cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemMax);
     });
 }
 
@@ -679,11 +691,12 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     e = cudaMemsetAsync(cnt, 0, count_bytes, stream);
     if (e != cudaSuccess) return cuda_err(e, "scratch reset");
     const int64_t sblocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    const size_t setup_smem = P.smem + ((P.ordered && !exact && g->d.work) ? kLatticeBytes : 0);
     if (g->d.kind == HG_KDTREE)
-        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, setup_smem, stream>>>(
             g->d, n, o, d, smax, P.starts, smem_nodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
     else
-        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, setup_smem, stream>>>(
             g->d, n, o, d, smax, P.starts, smem_nodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
     note_launches(1);
     if (P.ordered) {
@@ -692,12 +705,14 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     }
     if (P.splitting) {
         const int force = split == HG_SPLIT_FORCE ? 1 : 0;
+        // one warp per candidate ray: as many blocks as are resident at once
+        const unsigned pblocks = (unsigned)sm_count() * 4;
         if (g->d.kind == HG_KDTREE)
-            split_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+            split_kernel<HG_KDTREE><<<pblocks, 256, 0, stream>>>(
                 g->d, n, o, d, smax, P.starts, smem_nodes, P.work_total, P.counts, P.order, P.threads, force, P.segs,
                 P.seg_cap, P.seg_count, P.list, P.split_count);
         else
-            split_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, P.smem, stream>>>(
+            split_kernel<HG_OCTREE><<<pblocks, 256, 0, stream>>>(
                 g->d, n, o, d, smax, P.starts, smem_nodes, P.work_total, P.counts, P.order, P.threads, force, P.segs,
                 P.seg_cap, P.seg_count, P.list, P.split_count);
         note_launches(1);
@@ -753,8 +768,8 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
     note_launches(1);
     e = cudaGetLastError();
     if (e == cudaSuccess && P.splitting) {
-        if (mode == MODE_TAU) {
-            if (prec == HG_FP64)
+        if (mode == MODE_TAU || mode == MODE_TAUADJ) {
+            if ((prec & 1) == HG_FP64)
                 combine_kernel<MODE_TAU, HG_FP64><<<cblocks, 256, 0, stream>>>(
                     P.list, P.split_count, P.segs, P.part_acc, P.part_nc, P.part_last, P.part_st, A.kappa, A.tau,
                     A.ncross, A.status);
@@ -775,7 +790,7 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_err(e, "trace launch");
-    if (mode == MODE_TAU) P.traced = true;
+    if (mode == MODE_TAU || mode == MODE_TAUADJ) P.traced = true;
     return HG_OK;
 }
 
@@ -1096,6 +1111,36 @@ extern "C" hg_status hg_rays_trace(hg_rays *r, double kappa, const double *rho, 
     A.status = ray_status;
     A.rho_ext = rho;
     return walk_plan(*r, MODE_TAU, precision, A, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_rays_trace_gradient(hg_rays *r, double kappa, const double *rho, int32_t precision,
+                                            void *tau, int32_t *ncross, uint8_t *ray_status, const float *w,
+                                            int32_t grad_precision, void *grad_rho, hg_stream stream) {
+    if (!r) {
+        set_error("hg_rays_trace_gradient: null rays");
+        return HG_EINVAL;
+    }
+    if (precision != HG_FP64 && precision != HG_FP32K) {
+        set_error("precision must be HG_FP64 or HG_FP32K");
+        return HG_EINVAL;
+    }
+    if (grad_precision != 0 && grad_precision != 1) {
+        set_error("hg_rays_trace_gradient: grad_precision must be 0 (f64) or 1 (f32)");
+        return HG_EINVAL;
+    }
+    if (r->n > 0 && (!tau || !ncross || !w || !grad_rho)) {
+        set_error("hg_rays_trace_gradient: tau, ncross, w and grad_rho are required");
+        return HG_EINVAL;
+    }
+    TraceArgs A{};
+    A.kappa = kappa;
+    A.tau = tau;
+    A.ncross = ncross;
+    A.status = ray_status;
+    A.rho_ext = rho;
+    A.w = w;
+    A.grad = grad_rho;
+    return walk_plan(*r, MODE_TAUADJ, precision | (grad_precision << 1), A, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell,

@@ -207,15 +207,23 @@ __device__ __forceinline__ long long f32_key(float f) {
     return (fb >> 31) ? -(long long)mag : (long long)mag;
 }
 
+// Copy the work lattice (kWorkN^3 floats) into shared memory at lat.
+__device__ __forceinline__ void stage_lattice(const DevGrid &G, float *lat) {
+    const int4 *src = reinterpret_cast<const int4 *>(G.work);
+    int4 *dst = reinterpret_cast<int4 *>(lat);
+    for (int i = threadIdx.x; i < kWorkN * kWorkN * kWorkN / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
 // March of the path o + t k, t in [t0, t1], through the coarse work
-// lattice (expected crossings per unit length, G.work): a 3-D DDA
-// (Amanatides & Woo, 1987) in single precision.  Calls f(t, tn, rate, e)
+// lattice (expected crossings per unit length, G.work, or its copy in
+// shared memory lat): a 3-D DDA (Amanatides & Woo, 1987) in single
+// precision.  Calls f(t, tn, rate, e)
 // for every lattice cell the path crosses, [t, tn] being the part inside
 // it and e the work before it; returns the total work.  It only orders and
 // cuts the work; it never affects a result.
 template <class F>
-__device__ __forceinline__ float work_march(const DevGrid &G, const float *o, const float *k, float t0, float t1,
-                                            F &&f) {
+__device__ __forceinline__ float work_march(const DevGrid &G, const float *lat, const float *o, const float *k,
+                                            float t0, float t1, F &&f) {
     const int N = G.work_n;
     if (!G.work || N <= 0 || !(t1 > t0)) return 0.0f;
     float tmax[3], tdel[3];
@@ -249,7 +257,7 @@ __device__ __forceinline__ float work_march(const DevGrid &G, const float *o, co
         const int ax = (tmax[0] <= tmax[1]) ? (tmax[0] <= tmax[2] ? 0 : 2) : (tmax[1] <= tmax[2] ? 1 : 2);
         float tn = fminf(tmax[ax], t1);
         if (tn < t) tn = t;
-        const float rate = __ldg(G.work + c[0] + N * (c[1] + N * c[2]));
+        const float rate = lat[c[0] + N * (c[1] + N * c[2])];
         f(t, tn, rate, e);
         e += rate * (tn - t);
         t = tn;
@@ -275,7 +283,8 @@ __device__ __forceinline__ bool dlt0(double x) { return __double_as_longlong(x) 
 template <int KIND>
 __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned char *snodes, int n_smem,
                                               const double *__restrict__ o, const double *__restrict__ d,
-                                              const double *__restrict__ smax, int64_t r, bool estimate = false) {
+                                              const double *__restrict__ smax, int64_t r, bool estimate = false,
+                                              const float *lat = nullptr) {
     RayStart R;
     R.ik0 = R.ik1 = R.ik2 = 0.0;
     R.ktstart = 0;
@@ -373,7 +382,7 @@ __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned c
     if (estimate) {
         const float of[3] = {(float)oo[0], (float)oo[1], (float)oo[2]};
         const float kf[3] = {(float)kk[0], (float)kk[1], (float)kk[2]};
-        R.work = work_march(G, of, kf, (float)ts, t1f, [](float, float, float, float) {});
+        R.work = work_march(G, lat ? lat : G.work, of, kf, (float)ts, t1f, [](float, float, float, float) {});
     }
     return R;
 }
@@ -587,7 +596,8 @@ __device__ __forceinline__ int32_t cand_descend(const DevGrid &G, const unsigned
 }
 
 // Outputs and inputs of one walking launch.
-enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2 };
+// MODE_TAUADJ: the optical depth and the adjoint scatter in one walk.
+enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2, MODE_TAUADJ = 3 };
 struct WalkIO {
     const double *o;
     const double *d;
@@ -625,9 +635,14 @@ struct WalkIO {
 // ray - io.n_rays of a split ray (otherwise that code is compiled out).
 //   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
 //   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
+//   PREC (MODE_TAUADJ): bit 0 the optical depth's (HG_FP32K), bit 1 the gradient's (FP32).
 template <int KIND, int MODE, int PREC, class Src>
 __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem) {
     constexpr bool SEGS = Src::kSegments;
+    constexpr bool TAU = (MODE == MODE_TAU || MODE == MODE_TAUADJ);
+    constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_TAUADJ);
+    constexpr int TPREC = (MODE == MODE_TAUADJ) ? (PREC & 1) : PREC;         // HG_FP64 or HG_FP32K
+    constexpr int GPREC = (MODE == MODE_TAUADJ) ? ((PREC >> 1) & 1) : PREC;  // 0 FP64, 1 FP32 gradient
     const DevGrid *Gp = nullptr;
     int64_t ray = 0;
     int32_t max_steps = 0;
@@ -663,7 +678,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                 continue;
             }
             if (MODE == MODE_FILL) seg_base = (SEGS && ray >= io.n_rays) ? io.seg_base[ray - io.n_rays] : io.seg_off[r];
-            if (MODE == MODE_ADJ) wk = io.kappa * (double)io.w[r];
+            if (ADJ) wk = io.kappa * (double)io.w[r];
             if (rs == WALK_END) goto finish;
             C.id = S.cur;
             C.mode = CAND_ENTER;
@@ -697,8 +712,8 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             const bool skip = SEGS && (S.sg & SG_SKIP_FIRST) != 0;  // the segment before records this leaf
             if (SEGS) S.sg &= ~SG_SKIP_FIRST;
             if (rec && !skip) {
-                if (MODE == MODE_TAU) {
-                    if (PREC == HG_FP64) {
+                if (TAU) {
+                    if (TPREC == HG_FP64) {
                         const double rho = io.rho_ext ? __ldg(io.rho_ext + S.cur) : L.rho;
                         acc = acc + rho * ds;
                     } else {
@@ -709,7 +724,8 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                         comp32 = __fsub_rn(__fsub_rn(t, acc32), y);
                         acc32 = t;
                     }
-                } else if (MODE == MODE_FILL) {
+                }
+                if (MODE == MODE_FILL) {
                     const int64_t idx = seg_base + nc;
                     if (idx >= io.seg_cap) {
                         st |= HG_RAY_OVERFLOW;
@@ -720,9 +736,10 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                         static_cast<double *>(io.seg_ds)[idx] = ds;
                     else
                         static_cast<float *>(io.seg_ds)[idx] = __double2float_rn(ds);
-                } else {
+                }
+                if (ADJ) {
                     const double v = wk * ds;
-                    if (PREC == 0)
+                    if (GPREC == 0)
                         atomicAdd(static_cast<double *>(io.grad) + S.cur, v);
                     else
                         atomicAdd(static_cast<float *>(io.grad) + S.cur, __double2float_rn(v));
@@ -737,14 +754,14 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
     finish:
         if (SEGS && ray >= io.n_rays) {
             const int64_t sidx = ray - io.n_rays;
-            if (MODE == MODE_TAU) {
-                io.part_acc[sidx] = (PREC == HG_FP64) ? acc : (double)acc32;
+            if (TAU) {
+                io.part_acc[sidx] = (TPREC == HG_FP64) ? acc : (double)acc32;
                 io.part_nc[sidx] = nc;
             }
             io.part_last[sidx] = S.cur;
             io.part_st[sidx] = (uint8_t)st;
-        } else if (MODE == MODE_TAU) {
-            if (PREC == HG_FP64)
+        } else if (TAU) {
+            if (TPREC == HG_FP64)
                 static_cast<double *>(io.tau)[ray] = io.kappa * acc;
             else
                 static_cast<float *>(io.tau)[ray] = acc32;

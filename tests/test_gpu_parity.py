@@ -380,6 +380,37 @@ def test_prepared_rays_path_ends_and_gradient(hg, disk_grids, kind):
     np.testing.assert_allclose(got, 2.0 * np.asarray(seg_len), rtol=1e-12)
 
 
+@pytest.mark.parametrize("split", ["force", "off"])
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_fused_trace_and_gradient(hg, disk_grids, kind, split):
+    # optical depth, counts and the adjoint scatter in one walk, then an emission fill on the same plan
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    w = synth.adjoint_weights(17, o.shape[0])
+    ref = oracle.trace(tree, o, k, kappa=1.2, emit=True)
+    g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 1.2)
+    R = hg.prepare_rays(grid, _cuda(o), _cuda(k), split=split, schedule=3)
+    W = _cuda(w, torch.float32)
+    (tau, nc, st, g64), n = _launches(hg, lambda: R.trace_gradient(W, kappa=1.2, grad_precision="fp64"))
+    assert n == (2 if split == "force" else 1)  # walk (, combine)
+    np.testing.assert_array_equal(_np(nc), ref["ncross"])
+    np.testing.assert_array_equal(_np(st), ref["status"])
+    _check_tau(_np(tau), ref["tau"], TAU_RTOL_FP64)
+    np.testing.assert_allclose(_np(g64), g_ref, rtol=1e-12, atol=1e-300)
+    tau32, nc32, _, g32 = R.trace_gradient(W, kappa=1.2, precision="fp32k", grad_precision="fp32")
+    np.testing.assert_array_equal(_np(nc32), ref["ncross"])
+    _check_tau(_np(tau32), ref["tau"], TAU_RTOL_FP32K)
+    counts = np.bincount(ref["seg_cell"], minlength=tree.n_leaves).astype(np.float64)
+    u = 2.0 ** -24
+    gam = (counts + 1) * u / (1 - (counts + 1) * u)
+    assert (np.abs(_np(g32).astype(np.float64) - g_ref) <= gam * np.abs(g_ref) + 1e-30).all()
+    off = hg.scan_offsets(nc32)
+    cell, ds = R.fill(off)
+    np.testing.assert_array_equal(_np(cell), ref["seg_cell"])
+    np.testing.assert_array_equal(_np(ds), ref["seg_ds"])
+    R.free()
+
+
 def test_prepared_fill_needs_a_trace_when_paths_are_split(hg, disk_grids):
     model, grids, o, k = disk_grids
     grid, tree, _ = grids[0]
