@@ -595,6 +595,21 @@ __device__ __forceinline__ int32_t cand_descend(const DevGrid &G, const unsigned
     return descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg);
 }
 
+// Gradient scatter: a relaxed device-scope reduction (as atomicAdd without a
+// result), with an L2 evict-last policy so that the gradient lines stay in
+// L2 while the leaf-record gathers stream through it.
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void red_add_keep(float *a, float v, unsigned long long pol) {
+    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add_keep(double *a, double v, unsigned long long pol) {
+    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+
 // Outputs and inputs of one walking launch.
 // MODE_TAUADJ: the optical depth and the adjoint scatter in one walk.
 enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2, MODE_TAUADJ = 3 };
@@ -658,6 +673,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
     uint32_t st = 0;
     bool have = false;
     const float kappa32 = (float)io.kappa;
+    const unsigned long long keep = ADJ ? l2_evict_last_policy() : 0ULL;
     for (;;) {
         if (!have) {
             if (!src.next(ray, Gp, max_steps)) break;
@@ -740,9 +756,9 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                 if (ADJ) {
                     const double v = wk * ds;
                     if (GPREC == 0)
-                        atomicAdd(static_cast<double *>(io.grad) + S.cur, v);
+                        red_add_keep(static_cast<double *>(io.grad) + S.cur, v, keep);
                     else
-                        atomicAdd(static_cast<float *>(io.grad) + S.cur, __double2float_rn(v));
+                        red_add_keep(static_cast<float *>(io.grad) + S.cur, __double2float_rn(v), keep);
                 }
                 nc++;
             }
