@@ -47,9 +47,12 @@ UNIT = "rays/s"
 # wall's CSR range (2 x int64) + one neighbor id; per ray origin + direction in, tau + count + status out
 BYTES_PER_CROSSING = {"fp64": 48 + 8 + 16 + 4, "fp32k": 48 + 4 + 16 + 4}
 BYTES_PER_RAY = {"fp64": 48 + 8 + 4 + 1, "fp32k": 48 + 4 + 4 + 1}
-# the adjoint scatter fused into the same walk: an FP32 gradient read-modify-write per crossing, w per ray
+# fused into the same walk: the adjoint scatter (an FP32 gradient read-modify-write per crossing, w per
+# ray) and the emission staging (cell and ds per crossing, the first entry per ray)
 ADJ_BYTES_PER_CROSSING = 4 + 4
 ADJ_BYTES_PER_RAY = 4
+STAGE_BYTES_PER_CROSSING = {"fp64": 4 + 8, "fp32k": 4 + 4}
+STAGE_BYTES_PER_RAY = 4
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -267,15 +270,15 @@ def run_ours(args):
         out = {}
         for g in grids:
             G = g["grid"]
-            # one setup (first leaf, work-ordered queue, path segments) for the walks of these rays:
-            # optical depth, counts and the adjoint in one walk, then the emission fill
+            # one setup (first leaf, work-ordered queue, path segments) for these rays; one walk for
+            # the optical depth, counts, adjoint and the staged emission; then the emission copy
             R = hg.prepare_rays(G, O, K)
             g["grad"].zero_()
             if record:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            R.trace_gradient(W, kappa=1.0, precision=prec, grad=g["grad"], grad_precision="fp32",
-                             out=(g["tau"], g["nc"], g["st"]))
+            R.trace_stage(kappa=1.0, precision=prec, w=W, grad=g["grad"], grad_precision="fp32",
+                          out=(g["tau"], g["nc"], g["st"]))
             if record:
                 e1.record(stream)
                 kev.append((g["name"], e0, e1))
@@ -284,7 +287,7 @@ def run_ours(args):
             cap = g.get("cap")
             if cap is None:
                 cap = g["cap"] = int(off[-1].item())
-            cell, ds = R.fill(off, precision=prec, capacity=cap, status=g["st"])
+            cell, ds = R.emit_staged(off, capacity=cap, status=g["st"])
             _, rg = hg.sample_density(G, P)
             drho = hg.diff_stats(RT, rg)
             ptau, _, _ = hg.trace_rays(G, PA, PK, PL, kappa=1.0, precision="fp64", out=(g["ptau"], g["pnc"], None))
@@ -327,7 +330,8 @@ def run_ours(args):
     all_rays = sum_over_ranks(dist, rays_per_step * args.steps, dev)
     value = all_rays / (tot_ms / 1e3)
 
-    # dominant kernel: the fused optical-depth + adjoint walk; algorithmic bytes per launch / mean launch time
+    # dominant kernel: the walk for optical depth, adjoint and staged emission; algorithmic bytes per launch /
+    # mean launch time
     per = {}
     for name, e0, e1 in kev:
         per.setdefault(name, []).append(e0.elapsed_time(e1))
@@ -336,8 +340,8 @@ def run_ours(args):
     for g in grids:
         cr = int(g["nc"].sum().item())
         ms = statistics.mean(per[g["name"]])
-        byt = ((BYTES_PER_CROSSING[prec] + ADJ_BYTES_PER_CROSSING) * cr +
-               (BYTES_PER_RAY[prec] + ADJ_BYTES_PER_RAY) * n_rays)
+        byt = ((BYTES_PER_CROSSING[prec] + ADJ_BYTES_PER_CROSSING + STAGE_BYTES_PER_CROSSING[prec]) * cr +
+               (BYTES_PER_RAY[prec] + ADJ_BYTES_PER_RAY + STAGE_BYTES_PER_RAY) * n_rays)
         kern[g["name"]] = dict(leaves=g["grid"].n_leaves, build_s=round(g["build_s"], 2), load_s=round(g["load_s"], 2),
                                mean_ncross=cr / n_rays, trace_ms=ms, trace_rays_per_s=n_rays / ms * 1e3,
                                gcross_per_s=cr / ms / 1e6, algorithmic_bytes=byt,
@@ -354,8 +358,8 @@ def run_ours(args):
     achieved = tot_bytes / (tot_time / 1e3) / 1e9
     traffic = recorded_traffic(args.workload, prec)
     roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s", frac=round(achieved / peak, 4),
-                    traffic=traffic, kernel="trace_kernel, optical depth + adjoint walk over prepared rays "
-                                            "(hg_rays_trace_gradient)",
+                    traffic=traffic, kernel="trace_kernel, one walk for optical depth, adjoint and staged "
+                                            "emission over prepared rays (hg_rays_trace_stage)",
                     peak_source="measured" if "hbm_gbs" in peaks else "fallback")
 
     # e2e: the same step through the public API with host buffers (pinned), copies inside the timed region

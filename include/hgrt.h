@@ -311,6 +311,22 @@ hg_status hg_rays_trace(hg_rays *r, double kappa, const double *rho, int32_t pre
 hg_status hg_rays_trace_gradient(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
                                  int32_t *ncross, uint8_t *ray_status, const float *w, int32_t grad_precision,
                                  void *grad_rho, hg_stream stream);
+/* Single-pass emission.  hg_rays_trace_stage is hg_rays_trace (w NULL) or
+ * hg_rays_trace_gradient (w non-NULL) that also stages every emitted (cell,
+ * ds) in a pool owned by the handle: about stage_per_ray entries per ray
+ * (0 = 64) plus one 128-entry chunk per walking thread, kept until
+ * hg_rays_free.  hg_rays_emit_staged then copies each ray's crossings to
+ * seg_cell / seg_ds at seg_off (hg_scan_offsets over the staged ncross) --
+ * the same arrays hg_rays_fill writes, without a second walk.  When the pool
+ * was too small, the copy is skipped and a fill walk (launched either way,
+ * returning at once otherwise) does the emission: results never depend on
+ * the pool size.  stage_per_ray < 0 makes the pool exactly -stage_per_ray
+ * chunks (to exercise that fallback).  ds precision is the staged trace's. */
+hg_status hg_rays_trace_stage(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
+                              int32_t *ncross, uint8_t *ray_status, const float *w, int32_t grad_precision,
+                              void *grad_rho, int32_t stage_per_ray, hg_stream stream);
+hg_status hg_rays_emit_staged(hg_rays *r, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
+                              int64_t seg_capacity, uint8_t *ray_status, hg_stream stream);
 /* As hg_trace_fill; seg_off from hg_scan_offsets over the ncross of
  * hg_rays_trace (or hg_rays_trace_gradient) on the same rays. */
 hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,

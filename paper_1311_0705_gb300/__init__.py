@@ -110,6 +110,8 @@ _SIGS = {
     "hg_rays_prepare": (_S, [_V, _I64, _V, _V, _V, C.POINTER(TraceOpts), C.POINTER(_V), _V]),
     "hg_rays_trace": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V]),
     "hg_rays_trace_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V, C.c_int32, _V, _V]),
+    "hg_rays_trace_stage": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V, C.c_int32, _V, C.c_int32, _V]),
+    "hg_rays_emit_staged": (_S, [_V, _V, _V, _V, _I64, _V, _V]),
     "hg_rays_fill": (_S, [_V, C.c_int32, _V, _V, _V, _I64, _V, _V]),
     "hg_rays_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V]),
     "hg_rays_free": (None, [_V, _V]),
@@ -544,6 +546,62 @@ class Rays:
                                            _dptr(grad, gdt, (self.grid.n_leaves,), "grad"), _stream()),
                "hg_rays_trace_gradient")
         return tau, nc, st, grad
+
+    def trace_stage(self, kappa: float = 1.0, precision="fp64", w=None, rho=None, grad=None, grad_precision="fp32",
+                    out=None, status: bool = True, stage_per_ray: int = 0):
+        """hg_rays_trace_stage: tau, ncross, status (and, with w, the accumulated gradient) while
+        staging the emitted cells for emit_staged.  Returns (tau, nc, st, grad or None)."""
+        torch = _torch()
+        n = self.n
+        prec = {"fp64": FP64, "fp32k": FP32K}[precision]
+        tdt = torch.float64 if prec == FP64 else torch.float32
+        gp = {"fp64": 0, "fp32": 1}[grad_precision]
+        gdt = torch.float64 if gp == 0 else torch.float32
+        if out is None:
+            tau = torch.empty(n, dtype=tdt, device=self.device)
+            nc = torch.empty(n, dtype=torch.int32, device=self.device)
+            st = torch.empty(n, dtype=torch.uint8, device=self.device) if status else None
+        else:
+            tau, nc, st = out
+        pw = pg = None
+        if w is not None:
+            if grad is None:
+                grad = torch.zeros(self.grid.n_leaves, dtype=gdt, device=self.device)
+            pw = _dptr(w, torch.float32, (n,), "w")
+            pg = _dptr(grad, gdt, (self.grid.n_leaves,), "grad")
+        pr = None if rho is None else _dptr(rho, torch.float64, (self.grid.n_leaves,), "rho")
+        _check(_lib.hg_rays_trace_stage(self._h, float(kappa), pr, prec, _dptr(tau, tdt, (n,), "tau"),
+                                        _dptr(nc, torch.int32, (n,), "ncross"), _dptr(st, torch.uint8, (n,), "status"),
+                                        pw, gp, pg, int(stage_per_ray), _stream()), "hg_rays_trace_stage")
+        self._stage_prec = prec
+        return tau, nc, st, (grad if w is not None else None)
+
+    def emit_staged(self, seg_off, capacity: Optional[int] = None, status=None, out=None):
+        """hg_rays_emit_staged: the staged cells and lengths copied to their CSR slots."""
+        torch = _torch()
+        n = self.n
+        ddt = torch.float64 if getattr(self, "_stage_prec", FP64) == FP64 else torch.float32
+        if capacity is None:
+            capacity = int(seg_off[-1].item())
+        if out is None:
+            cell = torch.empty(max(capacity, 1), dtype=torch.int32, device=self.device)
+            ds = torch.empty(max(capacity, 1), dtype=ddt, device=self.device)
+        else:
+            cell, ds = out
+        _check(_lib.hg_rays_emit_staged(self._h, _dptr(seg_off, torch.int64, (n + 1,)), _dptr(cell), _dptr(ds, ddt),
+                                        int(capacity), _dptr(status, torch.uint8, (n,), "status"), _stream()),
+               "hg_rays_emit_staged")
+        return cell[:capacity], ds[:capacity]
+
+    def emit_single_pass(self, kappa: float = 1.0, precision="fp64", w=None, grad=None, grad_precision="fp32",
+                         stage_per_ray: int = 0):
+        """Optical depth (and gradient) with the emission in one walk plus a copy:
+        tau, ncross, status, seg_off, seg_cell, seg_ds (and grad)."""
+        tau, nc, st, g = self.trace_stage(kappa, precision, w=w, grad=grad, grad_precision=grad_precision,
+                                          stage_per_ray=stage_per_ray)
+        off = scan_offsets(nc)
+        cell, ds = self.emit_staged(off, status=st)
+        return dict(tau=tau, ncross=nc, status=st, seg_off=off, seg_cell=cell, seg_ds=ds, grad=g)
 
     def fill(self, seg_off, precision="fp64", capacity: Optional[int] = None, status=None, out=None):
         """Emitted cells and lengths (hg_rays_fill) at the offsets of a trace of these rays."""

@@ -47,6 +47,16 @@ struct TraceArgs {
     int32_t *part_last;
     uint8_t *part_st;
     const int64_t *seg_base;  // emission offset of each path segment (fill walks)
+    // emission staging (MODE_*_STAGE)
+    int32_t *stg_cell;
+    void *stg_ds;
+    uint32_t *stg_next;
+    uint32_t stg_nchunks;
+    unsigned long long *stg_ctr;
+    uint32_t *stg_start_ray;
+    uint32_t *stg_start_seg;
+    uint32_t *stg_overflow;
+    const uint32_t *run_if;  // when non-NULL, the walk runs only if *run_if != 0
 };
 
 // Stage the first n nodes of the (breadth-first) node list in shared memory.
@@ -435,6 +445,7 @@ struct GridRays {
 template <int KIND, int MODE, int PREC, int OCC>
 __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
+    if (A.run_if && *A.run_if == 0u) return;  // a fallback walk with nothing to do
     const int node_bytes = (KIND == HG_KDTREE) ? 16 : 32;
     stage_nodes(A.G.nodes, A.n_smem * node_bytes, smem);
     GridRays src;
@@ -474,6 +485,14 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.part_last = A.part_last;
     io.part_st = A.part_st;
     io.seg_base = A.seg_base;
+    io.stg_cell = A.stg_cell;
+    io.stg_ds = A.stg_ds;
+    io.stg_next = A.stg_next;
+    io.stg_nchunks = A.stg_nchunks;
+    io.stg_ctr = A.stg_ctr;
+    io.stg_start_ray = A.stg_start_ray;
+    io.stg_start_seg = A.stg_start_seg;
+    io.stg_overflow = A.stg_overflow;
     walk_loop<KIND, MODE, PREC>(src, io, smem, A.n_smem);
 }
 
@@ -482,13 +501,16 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
 typedef void (*KernelFn)(const TraceArgs);
 
 // Walking kernels by [kind][mode][prec][occupancy]; prec runs 0..1, and 0..3
-// for MODE_TAUADJ (optical depth and gradient precisions).
+// for MODE_TAUADJ and MODE_TAUADJ_STAGE (optical depth and gradient precisions).
+constexpr int kModes = 6;
+inline int mode_precs(int m) { return (m == MODE_TAUADJ || m == MODE_TAUADJ_STAGE) ? 4 : 2; }
 KernelFn pick_kernel(int kind, int mode, int prec, int occ) {
 #define HG_K(K, M, P) {&trace_kernel<K, M, P, 3>, &trace_kernel<K, M, P, 4>}
 #define HG_M(K, M) {HG_K(K, M, 0), HG_K(K, M, 1), {nullptr, nullptr}, {nullptr, nullptr}}
-#define HG_MA(K) {HG_K(K, 3, 0), HG_K(K, 3, 1), HG_K(K, 3, 2), HG_K(K, 3, 3)}
-    static const KernelFn table[2][4][4][2] = {{HG_M(0, 0), HG_M(0, 1), HG_M(0, 2), HG_MA(0)},
-                                                {HG_M(1, 0), HG_M(1, 1), HG_M(1, 2), HG_MA(1)}};
+#define HG_MA(K, M) {HG_K(K, M, 0), HG_K(K, M, 1), HG_K(K, M, 2), HG_K(K, M, 3)}
+    static const KernelFn table[2][kModes][4][2] = {
+        {HG_M(0, 0), HG_M(0, 1), HG_M(0, 2), HG_MA(0, 3), HG_M(0, 4), HG_MA(0, 5)},
+        {HG_M(1, 0), HG_M(1, 1), HG_M(1, 2), HG_MA(1, 3), HG_M(1, 4), HG_MA(1, 5)}};
 #undef HG_MA
 #undef HG_M
 #undef HG_K
@@ -559,8 +581,8 @@ void set_smem_limits() {
     static std::once_flag once;
     std::call_once(once, [] {
         for (int kd = 0; kd < 2; kd++)
-            for (int m = 0; m < 4; m++)
-                for (int p = 0; p < (m == MODE_TAUADJ ? 4 : 2); p++)
+            for (int m = 0; m < kModes; m++)
+                for (int p = 0; p < mode_precs(m); p++)
                     for (int oc = 3; oc <= 4; oc++)
                         cudaFuncSetAttribute(pick_kernel(kd, m, p, oc), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
@@ -610,6 +632,15 @@ struct hg_rays {
     int64_t *seg_base = nullptr;
     hg::SplitRec *list = nullptr;
     int64_t seg_cap = 0;
+    // emission staging, allocated by the first staged trace
+    unsigned char *stg = nullptr;
+    size_t stg_bytes = 0;
+    int32_t *stg_cell = nullptr;
+    void *stg_ds = nullptr;
+    uint32_t *stg_next = nullptr, *stg_start_ray = nullptr, *stg_start_seg = nullptr, *stg_overflow = nullptr;
+    unsigned long long *stg_ctr = nullptr;
+    uint32_t stg_nchunks = 0;
+    int stg_prec = -1;    // precision of the staged lengths; -1: nothing staged
 };
 
 namespace hg {
@@ -724,6 +755,129 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
 void free_plan(hg_rays &P, cudaStream_t stream) {
     if (P.scratch) cudaFreeAsync(P.scratch, stream);
     P.scratch = nullptr;
+    if (P.stg) cudaFreeAsync(P.stg, stream);
+    P.stg = nullptr;
+    P.stg_bytes = 0;
+}
+
+// Size the staging pool: per_ray entries per ray plus one chunk per walking
+// thread (each thread's last chunk is partly filled), at most 2^31 entries;
+// per_ray < 0: exactly -per_ray chunks.
+hg_status make_staging(hg_rays &P, int prec, int64_t per_ray, cudaStream_t stream) {
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    int64_t entries = per_ray < 0 ? -per_ray * (int64_t)kStageChunk
+                                  : P.n * per_ray + (P.threads + 1) * (int64_t)kStageChunk;
+    entries = std::min<int64_t>(entries, (int64_t)0x7fffffff - kStageChunk);
+    const int64_t nchunks = entries / kStageChunk;
+    entries = nchunks * kStageChunk;
+    const size_t dsz = prec == HG_FP64 ? sizeof(double) : sizeof(float);
+    const size_t b_cell = al((size_t)entries * sizeof(int32_t)), b_ds = al((size_t)entries * dsz);
+    const size_t b_next = al((size_t)nchunks * sizeof(uint32_t)), b_sr = al((size_t)P.n * sizeof(uint32_t));
+    const size_t b_ss = al((size_t)std::max<int64_t>(P.seg_cap, 1) * sizeof(uint32_t)), b_ctr = 256;
+    const size_t total = b_cell + b_ds + b_next + b_sr + b_ss + b_ctr;
+    if (total > P.stg_bytes) {
+        if (P.stg) cudaFreeAsync(P.stg, stream);
+        P.stg = nullptr;
+        P.stg_bytes = 0;
+        cudaError_t e = cudaMallocAsync((void **)&P.stg, total, stream);
+        if (e != cudaSuccess) {
+            P.stg = nullptr;
+            return cuda_err(e, "emission staging");
+        }
+        P.stg_bytes = total;
+    }
+    unsigned char *q = P.stg;
+    P.stg_cell = reinterpret_cast<int32_t *>(q);
+    q += b_cell;
+    P.stg_ds = q;
+    q += b_ds;
+    P.stg_next = reinterpret_cast<uint32_t *>(q);
+    q += b_next;
+    P.stg_start_ray = reinterpret_cast<uint32_t *>(q);
+    q += b_sr;
+    P.stg_start_seg = reinterpret_cast<uint32_t *>(q);
+    q += b_ss;
+    P.stg_ctr = reinterpret_cast<unsigned long long *>(q);
+    P.stg_overflow = reinterpret_cast<uint32_t *>(q + 8);
+    P.stg_nchunks = (uint32_t)nchunks;
+    cudaError_t e = cudaMemsetAsync(q, 0, 16, stream);
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "staging reset");
+}
+
+// Copy cnt staged entries starting at entry e (following the walking
+// thread's chunk chain) to the emission arrays at b, G lanes together (lane
+// g of the group, G a power of two dividing 32): each chunk piece is read
+// and written by consecutive lanes.  Entries at or beyond cap are dropped
+// (returns false then, on every lane of the group).
+template <int G, typename DS>
+__device__ __forceinline__ bool copy_staged_group(uint32_t e, int64_t cnt, int64_t b,
+                                                  const int32_t *__restrict__ cell, const DS *__restrict__ ds,
+                                                  const uint32_t *__restrict__ next, int32_t *out_cell, DS *out_ds,
+                                                  int64_t cap, int g) {
+    bool fit = true;
+    while (cnt > 0) {
+        const int64_t piece = std::min<int64_t>(cnt, (int64_t)(kStageChunk - (e & (kStageChunk - 1u))));
+        for (int64_t k = g; k < piece; k += G) {
+            if (b + k < cap) {
+                out_cell[b + k] = cell[e + k];
+                out_ds[b + k] = ds[e + k];
+            } else {
+                fit = false;
+            }
+        }
+        cnt -= piece;
+        b += piece;
+        if (cnt > 0) e = next[e >> kStageShift] << kStageShift;
+    }
+    return fit;
+}
+
+// Emission from the staging pool: each ray's crossings (or its segments',
+// in path order with the counts of the staged walk) copied to its CSR slot
+// by one warp.  Does nothing when the pool overflowed (the fill walk that
+// follows then does the emission).
+template <typename DS>
+__global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *__restrict__ starts,
+                                                     const int64_t *__restrict__ seg_off,
+                                                     const uint32_t *__restrict__ start_ray,
+                                                     const SplitRec *__restrict__ list,
+                                                     const unsigned long long *split_count,
+                                                     const uint32_t *__restrict__ start_seg,
+                                                     const int32_t *__restrict__ part_nc,
+                                                     const int32_t *__restrict__ cell, const DS *__restrict__ ds,
+                                                     const uint32_t *__restrict__ next, const uint32_t *overflow,
+                                                     int32_t *out_cell, DS *out_ds, int64_t cap, uint8_t *status) {
+    if (*overflow) return;
+    constexpr int G = 8;  // lanes per unsplit ray: four rays per warp in flight
+    const int lane = threadIdx.x & 31, g = lane & (G - 1);
+    const unsigned gmask = 0xffu << (lane & ~(G - 1));
+    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x / G);
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    for (int64_t r = g0; r < n; r += ngroups) {
+        if (starts[r].sg & SG_SPLIT) continue;
+        const int64_t b = seg_off[r], cnt = seg_off[r + 1] - b;
+        if (cnt <= 0) continue;
+        const bool fit = copy_staged_group<G>(start_ray[r], cnt, b, cell, ds, next, out_cell, out_ds, cap, g);
+        if (!__all_sync(gmask, fit) && status && g == 0) status[r] |= HG_RAY_OVERFLOW;
+    }
+    // split rays: one warp each, segments in path order
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t m = split_count ? (int64_t)*split_count : 0;
+    for (int64_t i = w0; i < m; i += nw) {
+        const SplitRec rec = list[i];
+        int64_t b = seg_off[rec.ray];
+        bool fit = true;
+        for (int j = 0; j < rec.count; j++) {
+            const int64_t cnt = part_nc[rec.first + j];
+            if (cnt > 0)
+                fit = copy_staged_group<32>(start_seg[rec.first + j], cnt, b, cell, ds, next, out_cell, out_ds, cap,
+                                            lane) &&
+                      fit;
+            b += cnt;
+        }
+        if (!__all_sync(0xffffffffu, fit) && status && lane == 0) status[rec.ray] |= HG_RAY_OVERFLOW;
+    }
 }
 
 // One walk over a plan.  A carries the outputs of the mode (and kappa, w,
@@ -756,6 +910,16 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
         A.part_st = P.part_st;
         A.seg_base = P.seg_base;
     }
+    if (mode == MODE_TAU_STAGE || mode == MODE_TAUADJ_STAGE) {
+        A.stg_cell = P.stg_cell;
+        A.stg_ds = P.stg_ds;
+        A.stg_next = P.stg_next;
+        A.stg_nchunks = P.stg_nchunks;
+        A.stg_ctr = P.stg_ctr;
+        A.stg_start_ray = P.stg_start_ray;
+        A.stg_start_seg = P.stg_start_seg;
+        A.stg_overflow = P.stg_overflow;
+    }
     cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_err(e, "queue reset");
     const unsigned cblocks =
@@ -768,7 +932,7 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
     note_launches(1);
     e = cudaGetLastError();
     if (e == cudaSuccess && P.splitting) {
-        if (mode == MODE_TAU || mode == MODE_TAUADJ) {
+        if (mode == MODE_TAU || mode == MODE_TAUADJ || mode == MODE_TAU_STAGE || mode == MODE_TAUADJ_STAGE) {
             if ((prec & 1) == HG_FP64)
                 combine_kernel<MODE_TAU, HG_FP64><<<cblocks, 256, 0, stream>>>(
                     P.list, P.split_count, P.segs, P.part_acc, P.part_nc, P.part_last, P.part_st, A.kappa, A.tau,
@@ -790,7 +954,8 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_err(e, "trace launch");
-    if (mode == MODE_TAU || mode == MODE_TAUADJ) P.traced = true;
+    if (mode == MODE_TAU || mode == MODE_TAUADJ || mode == MODE_TAU_STAGE || mode == MODE_TAUADJ_STAGE)
+        P.traced = true;
     return HG_OK;
 }
 
@@ -1141,6 +1306,86 @@ extern "C" hg_status hg_rays_trace_gradient(hg_rays *r, double kappa, const doub
     A.w = w;
     A.grad = grad_rho;
     return walk_plan(*r, MODE_TAUADJ, precision | (grad_precision << 1), A, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_rays_trace_stage(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
+                                         int32_t *ncross, uint8_t *ray_status, const float *w, int32_t grad_precision,
+                                         void *grad_rho, int32_t stage_per_ray, hg_stream stream) {
+    if (!r) {
+        set_error("hg_rays_trace_stage: null rays");
+        return HG_EINVAL;
+    }
+    if (precision != HG_FP64 && precision != HG_FP32K) {
+        set_error("precision must be HG_FP64 or HG_FP32K");
+        return HG_EINVAL;
+    }
+    if (w && grad_precision != 0 && grad_precision != 1) {
+        set_error("hg_rays_trace_stage: grad_precision must be 0 (f64) or 1 (f32)");
+        return HG_EINVAL;
+    }
+    if (r->n > 0 && (!tau || !ncross || (w && !grad_rho))) {
+        set_error("hg_rays_trace_stage: tau and ncross (and grad_rho with w) are required");
+        return HG_EINVAL;
+    }
+    if (r->n == 0) {
+        r->stg_prec = precision;
+        return HG_OK;
+    }
+    hg_status st = make_staging(*r, precision, stage_per_ray ? stage_per_ray : 64, (cudaStream_t)stream);
+    if (st != HG_OK) return st;
+    TraceArgs A{};
+    A.kappa = kappa;
+    A.tau = tau;
+    A.ncross = ncross;
+    A.status = ray_status;
+    A.rho_ext = rho;
+    A.w = w;
+    A.grad = grad_rho;
+    st = w ? walk_plan(*r, MODE_TAUADJ_STAGE, precision | (grad_precision << 1), A, (cudaStream_t)stream)
+           : walk_plan(*r, MODE_TAU_STAGE, precision, A, (cudaStream_t)stream);
+    r->stg_prec = (st == HG_OK) ? precision : -1;
+    return st;
+}
+
+extern "C" hg_status hg_rays_emit_staged(hg_rays *r, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
+                                         int64_t seg_capacity, uint8_t *ray_status, hg_stream stream) {
+    if (!r) {
+        set_error("hg_rays_emit_staged: null rays");
+        return HG_EINVAL;
+    }
+    if (r->stg_prec < 0) {
+        set_error("hg_rays_emit_staged: call hg_rays_trace_stage on these rays first");
+        return HG_EINVAL;
+    }
+    if (r->n > 0 && (!seg_off || (seg_capacity > 0 && (!seg_cell || !seg_ds)) || seg_capacity < 0)) {
+        set_error("hg_rays_emit_staged: bad segment arrays");
+        return HG_EINVAL;
+    }
+    if (r->n == 0) return HG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t gblocks = std::min<int64_t>((r->n * 8 + 255) / 256, (int64_t)sm_count() * 8);
+    if (r->stg_prec == HG_FP64)
+        gather_kernel<double><<<(unsigned)gblocks, 256, 0, s>>>(
+            r->n, r->starts, seg_off, r->stg_start_ray, r->list, r->splitting ? r->split_count : nullptr,
+            r->stg_start_seg, r->part_nc, r->stg_cell, static_cast<const double *>(r->stg_ds), r->stg_next,
+            r->stg_overflow, seg_cell, static_cast<double *>(seg_ds), seg_capacity, ray_status);
+    else
+        gather_kernel<float><<<(unsigned)gblocks, 256, 0, s>>>(
+            r->n, r->starts, seg_off, r->stg_start_ray, r->list, r->splitting ? r->split_count : nullptr,
+            r->stg_start_seg, r->part_nc, r->stg_cell, static_cast<const float *>(r->stg_ds), r->stg_next,
+            r->stg_overflow, seg_cell, static_cast<float *>(seg_ds), seg_capacity, ray_status);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e, "gather launch");
+    // the fill walk runs only when the staging pool overflowed
+    TraceArgs A{};
+    A.seg_off = seg_off;
+    A.seg_cell = seg_cell;
+    A.seg_ds = seg_ds;
+    A.seg_cap = seg_capacity;
+    A.status = ray_status;
+    A.run_if = r->stg_overflow;
+    return walk_plan(*r, MODE_FILL, r->stg_prec, A, s);
 }
 
 extern "C" hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell,

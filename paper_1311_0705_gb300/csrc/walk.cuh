@@ -612,7 +612,17 @@ __device__ __forceinline__ void red_add_keep(double *a, double v, unsigned long 
 
 // Outputs and inputs of one walking launch.
 // MODE_TAUADJ: the optical depth and the adjoint scatter in one walk.
-enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2, MODE_TAUADJ = 3 };
+// MODE_TAU_STAGE, MODE_TAUADJ_STAGE: the same, also staging every emitted
+// (cell, ds) for a gather into the emission arrays once the counts are known.
+enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2, MODE_TAUADJ = 3, MODE_TAU_STAGE = 4, MODE_TAUADJ_STAGE = 5 };
+
+// Emission staging: a pool of chunks of kStageChunk entries (cell, ds);
+// each walking thread appends the crossings of the rays and segments it
+// walks to its own chain of chunks, taking a new chunk from a global
+// counter when one fills.  Entry positions are stored shifted by one chunk
+// (position p is entry p - kStageChunk) so that 0 means "no chunk yet".
+constexpr int kStageShift = 7;
+constexpr uint32_t kStageChunk = 1u << kStageShift;
 struct WalkIO {
     const double *o;
     const double *d;
@@ -638,6 +648,15 @@ struct WalkIO {
     int32_t *part_last = nullptr;  // leaf the segment stopped in
     uint8_t *part_st = nullptr;    // partial status bits
     const int64_t *seg_base = nullptr;  // emission offset of each segment (MODE_FILL)
+    // staging (MODE_*_STAGE)
+    int32_t *stg_cell = nullptr;
+    void *stg_ds = nullptr;              // f64 or f32 (HG_FP32K) entries
+    uint32_t *stg_next = nullptr;        // chunk -> next chunk of the same thread
+    uint32_t stg_nchunks = 0;
+    unsigned long long *stg_ctr = nullptr;
+    uint32_t *stg_start_ray = nullptr;   // first entry of each unsplit ray
+    uint32_t *stg_start_seg = nullptr;   // first entry of each path segment
+    uint32_t *stg_overflow = nullptr;    // set when the pool ran out
 };
 
 // The walking loop of one thread.  Each iteration loads exactly one leaf
@@ -654,10 +673,12 @@ struct WalkIO {
 template <int KIND, int MODE, int PREC, class Src>
 __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem) {
     constexpr bool SEGS = Src::kSegments;
-    constexpr bool TAU = (MODE == MODE_TAU || MODE == MODE_TAUADJ);
-    constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_TAUADJ);
-    constexpr int TPREC = (MODE == MODE_TAUADJ) ? (PREC & 1) : PREC;         // HG_FP64 or HG_FP32K
-    constexpr int GPREC = (MODE == MODE_TAUADJ) ? ((PREC >> 1) & 1) : PREC;  // 0 FP64, 1 FP32 gradient
+    constexpr bool STAGE = (MODE == MODE_TAU_STAGE || MODE == MODE_TAUADJ_STAGE);
+    constexpr bool TAU = (MODE == MODE_TAU || MODE == MODE_TAUADJ || STAGE);
+    constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_TAUADJ || MODE == MODE_TAUADJ_STAGE);
+    constexpr bool TWO = (MODE == MODE_TAUADJ || MODE == MODE_TAUADJ_STAGE);
+    constexpr int TPREC = TWO ? (PREC & 1) : (ADJ ? HG_FP64 : PREC);  // HG_FP64 or HG_FP32K
+    constexpr int GPREC = TWO ? ((PREC >> 1) & 1) : PREC;             // 0 FP64, 1 FP32 gradient
     const DevGrid *Gp = nullptr;
     int64_t ray = 0;
     int32_t max_steps = 0;
@@ -672,6 +693,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
     double wk = 0.0;  // kappa * w for the adjoint
     uint32_t st = 0;
     bool have = false;
+    uint32_t sp = 0;  // staging: next entry position (shifted; 0 = no chunk)
     const float kappa32 = (float)io.kappa;
     const unsigned long long keep = ADJ ? l2_evict_last_policy() : 0ULL;
     for (;;) {
@@ -752,6 +774,33 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                         static_cast<double *>(io.seg_ds)[idx] = ds;
                     else
                         static_cast<float *>(io.seg_ds)[idx] = __double2float_rn(ds);
+                }
+                if (STAGE && sp != 0xffffffffu) {
+                    if ((sp & (kStageChunk - 1u)) == 0u) {
+                        const uint32_t c = (uint32_t)atomicAdd(io.stg_ctr, 1ULL);
+                        if (c >= io.stg_nchunks) {
+                            sp = 0xffffffffu;  // pool exhausted: the emission falls back to a fill walk
+                            *io.stg_overflow = 1u;
+                        } else {
+                            if (sp != 0u) io.stg_next[((sp - 1u) >> kStageShift) - 1u] = c;
+                            sp = (c + 1u) << kStageShift;
+                        }
+                    }
+                    if (sp != 0xffffffffu) {
+                        const uint32_t e = sp - kStageChunk;
+                        if (nc == 0) {
+                            if (SEGS && ray >= io.n_rays)
+                                io.stg_start_seg[ray - io.n_rays] = e;
+                            else
+                                io.stg_start_ray[ray] = e;
+                        }
+                        io.stg_cell[e] = S.cur;
+                        if (TPREC == HG_FP64)
+                            static_cast<double *>(io.stg_ds)[e] = ds;
+                        else
+                            static_cast<float *>(io.stg_ds)[e] = __double2float_rn(ds);
+                        sp++;
+                    }
                 }
                 if (ADJ) {
                     const double v = wk * ds;

@@ -411,6 +411,41 @@ def test_fused_trace_and_gradient(hg, disk_grids, kind, split):
     R.free()
 
 
+@pytest.mark.parametrize("split", ["force", "auto", "off"])
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_single_pass_emission_bit_exact(hg, disk_grids, kind, split):
+    # the trace stages every emitted cell; a copy puts them at the scanned offsets: the whole
+    # sequences and lengths must be the oracle's, with or without the gradient in the same walk
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    w = synth.adjoint_weights(23, o.shape[0])
+    ref = oracle.trace(tree, o, k, kappa=0.9, emit=True)
+    g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 0.9)
+    R = hg.prepare_rays(grid, _cuda(o), _cuda(k), split=split, schedule=3)
+    W = _cuda(w, torch.float32)
+    for prec, with_w in (("fp64", True), ("fp32k", False), ("fp64", False), ("fp32k", True)):
+        out = R.emit_single_pass(kappa=0.9, precision=prec, w=W if with_w else None, grad_precision="fp64")
+        _same_emission(out, ref, prec)
+        if with_w:
+            np.testing.assert_allclose(_np(out["grad"]), g_ref, rtol=1e-12, atol=1e-300)
+    R.free()
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_single_pass_emission_pool_overflow_falls_back(hg, disk_grids, kind):
+    # a pool of 3 chunks cannot hold the crossings: the copy is skipped and the fill walk emits
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    a, kk, L = synth.endpoint_paths(81, 3001)
+    ref = oracle.trace(tree, a, kk, smax=L, emit=True)
+    R = hg.prepare_rays(grid, _cuda(a), _cuda(kk), _cuda(L), split="force")
+    out = R.emit_single_pass(stage_per_ray=-3)
+    _same_emission(out, ref, "fp64")
+    out2 = R.emit_single_pass()  # the default pool holds them
+    _same_emission(out2, ref, "fp64")
+    R.free()
+
+
 def test_prepared_fill_needs_a_trace_when_paths_are_split(hg, disk_grids):
     model, grids, o, k = disk_grids
     grid, tree, _ = grids[0]
