@@ -221,6 +221,38 @@ WORKLOADS = {
 }
 
 
+def matched_kd(hg, model, grids, P, PA, PK, PL, RT, TT):
+    """k-d tree with the octree's leaf count (within 5 %) by bisection of the mass threshold, and its
+    Delta-rho / Delta-tau on the same points and paths as the timed step."""
+    target = next(g for g in grids if g["kind"] == 0)["host"].n_leaves
+    _, bp, _, _ = synth.workload_disk_1e6(1)
+    lo, hi = math.log(bp.delta_max) - math.log(8.0), math.log(bp.delta_max)
+    best = None
+    t0 = time.time()
+    for _ in range(12):
+        dm = math.exp(0.5 * (lo + hi))
+        _, bpi, _, _ = synth.workload_disk_1e6(1, delta_max=dm)
+        H = hg.build_grid(model, bpi)
+        r = H.n_leaves / target
+        if best is None or abs(r - 1) < abs(best[2] - 1):
+            best = (dm, H, r)
+        if abs(r - 1) <= 0.05:
+            break
+        if r > 1:
+            lo = math.log(dm)
+        else:
+            hi = math.log(dm)
+    dm, H, r = best
+    G = hg.load_grid(H)
+    _, rg = hg.sample_density(G, P)
+    ptau, _, _ = hg.trace_rays(G, PA, PK, PL, kappa=1.0, precision="fp64")
+    drho = hg.diff_stats(RT, rg)
+    dtau = hg.diff_stats(TT, ptau)
+    return dict(delta_max=dm, leaves=H.n_leaves, leaves_over_octree=round(r, 4),
+                delta_rho=float(drho[2].item()), delta_tau=float(dtau[2].item()),
+                search_s=round(time.time() - t0, 1))
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -393,6 +425,12 @@ def run_ours(args):
         e2e = dict(value=sum_over_ranks(dist, rays_per_step * args.steps, dev) / (e_ms / 1e3), unit=UNIT,
                    h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
 
+    # quality at equal cell counts (outside the timed region): a k-d tree whose mass threshold is bisected
+    # until its leaf count is within 5 % of the octree's, with its Delta-rho and Delta-tau
+    matched = None
+    if world == 1 and not args.no_matched and args.workload == "disk-1e6":
+        matched = matched_kd(hg, model, grids, P, PA, PK, PL, RT, TT)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(model, grids, o, k, pts, pa, pk, pl, w, sample=args.cpu_sample)
@@ -402,7 +440,7 @@ def run_ours(args):
                 dtype="f64" if prec == "fp64" else "f32+f64", data="synthetic",
                 config=dict(workload=args.workload, description=desc, rays_per_grid=n_rays, points=n_pts,
                             paths=n_paths, precision=prec, l2="flushed between steps (512 MB write)",
-                            grids=kern),
+                            grids=kern, kd_matched_to_octree=matched),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
                 clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
     if rank == 0:
@@ -737,6 +775,8 @@ def main(argv=None):
     ap.add_argument("--validate", action="store_true", help="validate grid descriptions at load")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-matched", action="store_true",
+                    help="skip the k-d tree built to the octree's leaf count (quality at equal N_cells)")
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":

@@ -647,3 +647,54 @@ def test_torus_full_size_sequences_sampled(hg, torus_full):
     o, k = synth.emission_rays(seed, 20000)
     _compare(hg, grid, tree, o, k)
     _compare(hg, grid, tree, o, k, precision="fp32k")
+
+
+def test_torus_full_size_gradient(hg, torus_full):
+    # the adjoint at full size (1e7 rays, ~8.4e6 leaves): FP64 reductions against an FP64 accumulation of
+    # the emitted segments (whose cells and lengths match the oracle bit for bit in the tests above), FP32
+    # reductions within gamma_{n+1} of it per cell, and central differences on 100 cells
+    model, bp, H, seed = torus_full
+    grid = hg.load_grid(H)
+    n = 10_000_000
+    o, k = synth.emission_rays(seed, n)
+    w = synth.adjoint_weights(seed + 3, n)
+    O, K, W = _cuda(o), _cuda(k), _cuda(w, torch.float32)
+    g64 = hg.tau_gradient(grid, O, K, W, grad_precision="fp64")
+    g32 = hg.tau_gradient(grid, O, K, W, grad_precision="fp32")
+    R = hg.prepare_rays(grid, O, K)
+    out = R.emit_single_pass()
+    nc = out["ncross"].long()
+    cell = out["seg_cell"].long()
+    ray_of_seg = torch.repeat_interleave(torch.arange(n, device="cuda"), nc)
+    terms = W.double()[ray_of_seg] * out["seg_ds"]
+    g_ref = torch.zeros(grid.n_leaves, dtype=torch.float64, device="cuda").index_add_(0, cell, terms)
+    counts = torch.bincount(cell, minlength=grid.n_leaves).double()
+    del ray_of_seg, terms, out
+    R.free()
+    # all terms are positive: two FP64 orders differ by at most n_c ulps relative
+    err64 = (g64 - g_ref).abs()
+    assert bool((err64 <= 2.3e-16 * (counts + 1) * g_ref + 1e-300).all()), float((err64 / g_ref.clamp_min(1e-300)).max())
+    u = 2.0 ** -24
+    gam = (counts + 1) * u / (1 - (counts + 1) * u)
+    err32 = (g32.double() - g_ref).abs()
+    assert bool((err32 <= gam * g_ref + 1e-30).all())
+    hit = torch.nonzero(g_ref > 0).squeeze(1)
+    rel32 = (err32[hit] / g_ref[hit])
+    assert float(rel32.median()) < 1e-6
+    # central differences: tau is linear in rho, and rays that miss the cell give identical bits both ways
+    rng = np.random.default_rng(5)
+    gh = _np(g64)
+    hit_np = _np(hit)
+    pw = gh[hit_np] / gh[hit_np].sum()
+    cells = np.concatenate([rng.choice(hit_np, 50, replace=False), rng.choice(hit_np, 50, replace=False, p=pw)])
+    rho = torch.tensor(H.leaf_rho, dtype=torch.float64, device="cuda")
+    Wd = W.double()
+    for c in cells:
+        h = 1e-3 * max(1.0, float(rho[c]))
+        rp, rm = rho.clone(), rho.clone()
+        rp[c] += h
+        rm[c] -= h
+        tp, _ = hg.trace_rays_rho(grid, O, K, rp)
+        tm, _ = hg.trace_rays_rho(grid, O, K, rm)
+        fd = float((Wd * (tp - tm)).sum()) / (2 * h)
+        assert fd == pytest.approx(gh[c], rel=1e-6)
