@@ -83,6 +83,8 @@ def _load():
             "or_brute_locate_batch": (None, [_P, C.c_int64, _D, _D, _I64, _I64]),
             "or_trace_batch": (C.c_int32, [_P, C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _D, _I64, _I32,
                                            _I64, _I32, _D]),
+            "or_interact_batch": (C.c_int32, [_P, C.c_int64, _D, _D, _D, C.c_double, _D, C.c_int64, _I64, _D,
+                                              _I64, _I32]),
             "or_brute_sequence": (C.c_int64, [_P, _D, _D, C.c_double, C.c_double, _I32, _D, _D, C.c_int64]),
             "or_quad_poly": (C.c_double, [_D, C.c_int, C.c_double, C.c_double, C.c_int]),
             "or_tau_true_batch": (None, [C.POINTER(_Model), C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D]),
@@ -297,6 +299,42 @@ def _threads(threads: Optional[int]) -> int:
     if threads is None or threads <= 0:
         return max(1, os.cpu_count() or 1)
     return int(threads)
+
+
+def interact(tree: Tree, o, k, tau_int, smax=None, kappa: float = 1.0, max_steps: Optional[int] = None,
+             threads: Optional[int] = None) -> dict:
+    """Interaction-point search in the oracle: for each path, the leaf in which the accumulated
+    optical depth first reaches tau_int (-1 when the path ends first), the path parameter t of the
+    interaction inside it (or of the path end), the recorded segments walked, and the status."""
+    lib = _load()
+    o = _f64(o).reshape(-1, 3)
+    k = _f64(k).reshape(-1, 3)
+    ti = _f64(tau_int).reshape(-1)
+    n = o.shape[0]
+    sm = None if smax is None else _f64(smax).reshape(-1)
+    ms = default_max_steps(tree.n_leaves) if max_steps is None else int(max_steps)
+    cell = np.empty(n, np.int64)
+    t = np.empty(n, np.float64)
+    nc = np.empty(n, np.int64)
+    st = np.empty(n, np.int32)
+    nt = min(_threads(threads), max(1, n // 256))
+    chunks = np.linspace(0, n, nt + 1).astype(np.int64)
+
+    def run(c):
+        a, b = int(chunks[c]), int(chunks[c + 1])
+        if b <= a:
+            return
+        lib.or_interact_batch(tree.handle, b - a, _ptr(o[a:], C.c_double), _ptr(k[a:], C.c_double),
+                              _ptr(None if sm is None else sm[a:], C.c_double), float(kappa),
+                              _ptr(ti[a:], C.c_double), ms, _ptr(cell[a:], C.c_int64), _ptr(t[a:], C.c_double),
+                              _ptr(nc[a:], C.c_int64), _ptr(st[a:], C.c_int32))
+
+    if nt == 1:
+        run(0)
+    else:
+        with _cf.ThreadPoolExecutor(nt) as ex:
+            list(ex.map(run, range(nt)))
+    return dict(cell=cell, t=t, ncross=nc, status=st)
 
 
 def trace(tree: Tree, o, k, smax=None, kappa: float = 1.0, emit: bool = False, max_steps: Optional[int] = None,

@@ -25,6 +25,10 @@
  *     exit is found by top-down relocation from the root after every step
  *     (the traditional method the paper contrasts with neighbor lists,
  *     Sect. 2.3), never by neighbor lists;
+ *   - the interaction-point search: the same walk stopped in the leaf where
+ *     the accumulated optical depth first reaches a drawn tau_int, with the
+ *     time inside it from the linear growth of tau across the leaf (the step
+ *     that follows the path in the Monte Carlo loop, Sect. 2.3);
  *   - brute-force references: point location by a linear scan over all
  *     leaves, and the crossed-cell list from every leaf's slab interval;
  *   - the true optical depth along a path by adaptive Gauss-Kronrod
@@ -592,6 +596,126 @@ int32_t or_trace_batch(const or_tree *T, int64_t n, const double *o, const doubl
                               sc, sd, cap);
         tau[i] = kappa * S;
         ncross[i] = nc;
+        if (status) status[i] = st;
+        all |= st;
+    }
+    return all;
+}
+
+/* Interaction-point search (the step after the path in the Monte Carlo loop,
+ * Sect. 2.3): walk as or_trace_one, accumulating S = sum rho*ds left to
+ * right, and stop in the first recorded segment after which kappa*S >= tau_int.
+ * Inside that leaf (entered at t_cur, left at t_exit) the interaction time
+ * solves kappa*S_before + kappa*rho*(t - t_cur) = tau_int:
+ *   a = tau_int - kappa*S_before; b = kappa*rho;
+ *   t = t_cur + a/b when a > 0 and b > 0, else t_cur; t = min(t, t_exit).
+ * *cell = the leaf id, *t = that time, *ncross = recorded segments up to and
+ * including it.  A path that ends (domain exit, s_max) first gives
+ * *cell = -1 and *t = its end time. */
+static int or_interact_one(const or_tree *T, const double *o, const double *k, int has_smax, double smax,
+                           double kappa, double tau_int, int64_t max_steps, int64_t *cell, double *t_out,
+                           int64_t *ncross)
+{
+    *cell = -1;
+    *t_out = 0.0;
+    *ncross = 0;
+    for (int a = 0; a < 3; a++)
+        if (!isfinite(o[a]) || !isfinite(k[a])) return OR_RAY_BADINPUT;
+    if (k[0] == 0.0 && k[1] == 0.0 && k[2] == 0.0) return OR_RAY_BADINPUT;
+    if (has_smax && isnan(smax)) return OR_RAY_BADINPUT;
+    if (isnan(tau_int)) return OR_RAY_BADINPUT;
+    const double *dlo = T->lo, *dhi = T->hi;
+    double invk[3];
+    for (int a = 0; a < 3; a++) invk[a] = (k[a] != 0.0) ? 1.0 / k[a] : 0.0;
+    double t_start = 0.0, t_out_dom = INFINITY;
+    int entry = -1;
+    for (int a = 0; a < 3; a++) {
+        if (k[a] == 0.0) {
+            if (o[a] < dlo[a] || o[a] > dhi[a]) return 0;
+            continue;
+        }
+        double tn = ((k[a] > 0.0 ? dlo[a] : dhi[a]) - o[a]) * invk[a];
+        double tf = ((k[a] > 0.0 ? dhi[a] : dlo[a]) - o[a]) * invk[a];
+        if (tn > t_start) { t_start = tn; entry = a; }
+        if (tf < t_out_dom) t_out_dom = tf;
+    }
+    if (!(t_start < t_out_dom)) return 0;
+    if (has_smax && !(t_start < smax)) return 0;
+    double p[3];
+    if (entry < 0) {
+        p[0] = o[0]; p[1] = o[1]; p[2] = o[2];
+    } else {
+        for (int a = 0; a < 3; a++) {
+            if (a == entry) { p[a] = (k[a] > 0.0) ? dlo[a] : dhi[a]; continue; }
+            double v = o[a] + k[a] * t_start;
+            if (v < dlo[a]) v = dlo[a];
+            if (v > dhi[a]) v = dhi[a];
+            p[a] = v;
+        }
+    }
+    int64_t cur = or_locate(T, p, k);
+    if (cur < 0) return 0;
+    double t_cur = t_start, S = 0.0;
+    int64_t steps = 0;
+    for (;;) {
+        if (steps >= max_steps) { *t_out = t_cur; return OR_RAY_STEPLIMIT; }
+        steps++;
+        int64_t nd = T->leaf_node[cur];
+        const double *lo = T->lo + 3 * nd, *hi = T->hi + 3 * nd;
+        double t_ex = INFINITY;
+        int ax = -1;
+        for (int a = 0; a < 3; a++) {
+            if (k[a] == 0.0) continue;
+            double w = (k[a] > 0.0) ? hi[a] : lo[a];
+            double t = (w - o[a]) * invk[a];
+            if (t < t_ex) { t_ex = t; ax = a; }
+        }
+        if (has_smax && smax < t_ex) { t_ex = smax; ax = -1; }
+        if (t_ex < t_cur) t_ex = t_cur;
+        double ds = t_ex - t_cur;
+        if (ds != 0.0) {
+            const double rho = T->rho[nd];
+            const double S_new = S + rho * ds;
+            (*ncross)++;
+            if (kappa * S_new >= tau_int) {
+                const double a = tau_int - kappa * S;
+                const double b = kappa * rho;
+                double t = t_cur;
+                if (a > 0.0 && b > 0.0) t = t_cur + a / b;
+                if (t > t_ex) t = t_ex;
+                *cell = cur;
+                *t_out = t;
+                return 0;
+            }
+            S = S_new;
+        }
+        t_cur = t_ex;
+        *t_out = t_cur;
+        if (ax < 0) return 0;
+        double wall = (k[ax] > 0.0) ? hi[ax] : lo[ax];
+        if (wall == ((k[ax] > 0.0) ? dhi[ax] : dlo[ax])) return 0;
+        for (int b = 0; b < 3; b++) {
+            if (b == ax) { p[b] = wall; continue; }
+            double v = o[b] + k[b] * t_ex;
+            if (v < lo[b]) v = lo[b];
+            if (v > hi[b]) v = hi[b];
+            p[b] = v;
+        }
+        if (!or_in_box(dlo, dhi, p, k, dlo, dhi)) return 0;
+        int64_t nxt = or_locate(T, p, k);
+        if (nxt < 0) return OR_RAY_LOST;
+        cur = nxt;
+    }
+}
+
+int32_t or_interact_batch(const or_tree *T, int64_t n, const double *o, const double *k, const double *smax,
+                          double kappa, const double *tau_int, int64_t max_steps, int64_t *cell, double *t,
+                          int64_t *ncross, int32_t *status)
+{
+    int32_t all = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int st = or_interact_one(T, o + 3 * i, k + 3 * i, smax != NULL, smax ? smax[i] : 0.0, kappa, tau_int[i],
+                                 max_steps, cell + i, t + i, ncross + i);
         if (status) status[i] = st;
         all |= st;
     }

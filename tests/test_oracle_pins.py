@@ -417,3 +417,71 @@ def test_adjoint_matches_central_differences(disk_small):
             vals.append(np.dot(w, oracle.trace(tw, o, k, kappa=kappa)["tau"]))
         fd = (vals[0] - vals[1]) / (2 * hstep)
         assert fd == pytest.approx(g[c], rel=1e-7, abs=1e-9)
+
+
+# ----------------------------------------------------------------------------- interaction points
+
+def test_interaction_uniform_closed_form():
+    # uniform rho0: the interaction lies at t = tau_int / (kappa rho0) along a unit direction, in the leaf
+    # containing that point (brute force); paths too short end at the exact chord without interaction
+    rho0, kappa = 2.5, 1.5
+    m = synth.make_const(rho0)
+    t = oracle.build_tree(m, _bp(kind=synth.TREE_KD, delta_max=1.0 / 200, max_level=8))
+    n = 400
+    o, k = synth.emission_rays(6, n)
+    chord = np.array([float(_exact_chord(o[i], k[i])) for i in range(n)])
+    f = np.random.default_rng(2).uniform(0.02, 1.5, n)
+    ti = f * kappa * rho0 * chord
+    r = oracle.interact(t, o, k, ti, kappa=kappa)
+    assert (r["status"] == 0).all()
+    inside = f < 1 - 1e-9
+    np.testing.assert_allclose(r["t"][inside], ti[inside] / (kappa * rho0), rtol=1e-12)
+    pts = o[inside] + k[inside] * r["t"][inside][:, None]
+    ref, hits = oracle.brute_locate(t, pts, k[inside])
+    assert (hits == 1).all()
+    np.testing.assert_array_equal(r["cell"][inside], ref)
+    out = f > 1 + 1e-9
+    assert (r["cell"][out] == -1).all()
+    np.testing.assert_allclose(r["t"][out], chord[out], rtol=1e-12)
+
+
+def test_interaction_matches_prefix_sums_of_the_path(disk_small):
+    # disk grid: the walk stops in the first emitted segment at which kappa * (running sum of rho*ds, left
+    # to right) reaches tau_int; the solved t lies in that leaf's slab interval and reproduces tau_int
+    model, bp, t, seed = disk_small
+    n = 300
+    o, k = synth.emission_rays(seed + 7, n)
+    kappa = 1.3
+    r = oracle.trace(t, o, k, kappa=kappa, emit=True)
+    ti = np.random.default_rng(9).uniform(0.0, 1.2, n) * r["tau"]
+    q = oracle.interact(t, o, k, ti, kappa=kappa)
+    assert (q["status"] == 0).all()
+    for i in range(n):
+        a, b = r["seg_off"][i], r["seg_off"][i + 1]
+        cells, ds = r["seg_cell"][a:b], r["seg_ds"][a:b]
+        rho = t.leaf_rho[cells]
+        S = np.cumsum(rho * ds)
+        hit = np.nonzero(kappa * S >= ti[i])[0]
+        if hit.size == 0:
+            assert q["cell"][i] == -1 and q["ncross"][i] == b - a
+            continue
+        j = int(hit[0])
+        assert q["cell"][i] == cells[j] and q["ncross"][i] == j + 1
+        bc, tin, bds = oracle.brute_sequence(t, o[i], k[i], 0.0, 2 * float(_exact_chord(o[i], k[i])))
+        m = np.nonzero(bc == cells[j])[0][0]
+        t_in, t_out = tin[m], tin[m] + bds[m]
+        assert t_in - 1e-12 <= q["t"][i] <= t_out + 1e-12
+        S_before = S[j - 1] if j else 0.0
+        assert kappa * (S_before + rho[j] * (q["t"][i] - t_in)) == pytest.approx(ti[i], rel=1e-9, abs=1e-12)
+
+
+def test_interaction_nonpositive_and_nan_tau(disk_small):
+    model, bp, t, seed = disk_small
+    n = 20
+    o, k = synth.emission_rays(seed + 8, n)
+    r = oracle.trace(t, o, k, emit=True)
+    q = oracle.interact(t, o, k, np.full(n, -1.0))
+    np.testing.assert_array_equal(q["cell"], r["seg_cell"][r["seg_off"][:-1]])
+    assert (q["t"] == 0.0).all() and (q["ncross"] == 1).all()
+    q2 = oracle.interact(t, o, k, np.full(n, np.nan))
+    assert (q2["status"] == oracle.RAY_BADINPUT).all() and (q2["cell"] == -1).all()
