@@ -268,6 +268,24 @@ hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o, const doub
                         const hg_trace_opts *opts, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
                         int64_t seg_capacity, uint8_t *ray_status, hg_stream stream);
 
+/* Interaction-point search (the step that follows the path in the Monte
+ * Carlo loop of Sect. 2.3): each path is walked as in hg_trace_rays, in FP64,
+ * and stops in the first recorded segment after which kappa * (sum of
+ * rho*ds, left to right) >= tau_int[i].  Inside that leaf, entered at t_in
+ * and left at t_exit, the interaction time solves the linear growth of tau:
+ *   a = tau_int - kappa*S_before, b = kappa*rho,
+ *   t = t_in + a/b when a > 0 and b > 0, else t_in;  t = min(t, t_exit).
+ * Outputs: cell[i] the leaf (-1 when the path ends first), t[i] the
+ * interaction time (else the path's end time, 0 for a path that misses the
+ * grid), ncross[i] the recorded segments walked including the interaction
+ * leaf, ray_status[i] as for hg_trace_rays (HG_RAY_BADINPUT also for a NaN
+ * tau_int).  tau_int dev f64[n] (the caller draws -ln u); cell dev i32[n],
+ * t dev f64[n], ncross dev i32[n].  Paths are never split into segments
+ * here (where one stops depends on everything before). */
+hg_status hg_find_interactions(const hg_grid *g, int64_t n, const double *o, const double *d, const double *s_max,
+                               double kappa, const double *tau_int, const hg_trace_opts *opts, int32_t *cell,
+                               double *t, int32_t *ncross, uint8_t *ray_status, hg_stream stream);
+
 /* Grid density at points (Sect. 3.2, rho_g): top-down location with the
  * half-open rule above for a zero direction; cell = -1 and rho = 0 for
  * points outside the domain.  pts dev f64[n][3], cell dev i32[n] (or

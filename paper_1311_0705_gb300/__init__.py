@@ -107,6 +107,8 @@ _SIGS = {
     "hg_trace_fill": (_S, [_V, _I64, _V, _V, _V, C.POINTER(TraceOpts), _V, _V, _V, _I64, _V, _V]),
     "hg_sample_density": (_S, [_V, _I64, _V, _V, _V, _V]),
     "hg_tau_gradient": (_S, [_V, _I64, _V, _V, _V, C.c_double, _V, C.c_int32, _V, C.POINTER(TraceOpts), _V]),
+    "hg_find_interactions": (_S, [_V, _I64, _V, _V, _V, C.c_double, _V, C.POINTER(TraceOpts), _V, _V, _V, _V,
+                                  _V]),
     "hg_rays_prepare": (_S, [_V, _I64, _V, _V, _V, C.POINTER(TraceOpts), C.POINTER(_V), _V]),
     "hg_rays_trace": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V]),
     "hg_rays_trace_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V, C.c_int32, _V, _V]),
@@ -425,6 +427,28 @@ def trace_rays_rho(grid: Grid, o, d, rho, s_max=None, kappa: float = 1.0, precis
                                   _dptr(rho, torch.float64, (grid.n_leaves,), "rho"), C.byref(op), _dptr(tau),
                                   _dptr(nc), None, _stream()), "hg_trace_rays_rho")
     return tau, nc
+
+
+def find_interactions(grid: Grid, o, d, tau_int, s_max=None, kappa: float = 1.0, out=None, **opt):
+    """Interaction points (hg_find_interactions): for each path the leaf where the accumulated optical
+    depth reaches tau_int (-1 if it ends first), the path parameter t there (or of the path end), the
+    segments walked and the status."""
+    torch = _torch()
+    n, po, pd, ps = _rays(o, d, s_max)
+    op = _opts("fp64", **opt)
+    if out is None:
+        cell = torch.empty(n, dtype=torch.int32, device=o.device)
+        t = torch.empty(n, dtype=torch.float64, device=o.device)
+        nc = torch.empty(n, dtype=torch.int32, device=o.device)
+        st = torch.empty(n, dtype=torch.uint8, device=o.device)
+    else:
+        cell, t, nc, st = out
+    _check(_lib.hg_find_interactions(grid.handle, n, po, pd, ps, float(kappa),
+                                     _dptr(tau_int, torch.float64, (n,), "tau_int"), C.byref(op),
+                                     _dptr(cell, torch.int32, (n,), "cell"), _dptr(t, torch.float64, (n,), "t"),
+                                     _dptr(nc, torch.int32, (n,), "ncross"), _dptr(st, torch.uint8, (n,), "status"),
+                                     _stream()), "hg_find_interactions")
+    return cell, t, nc, st
 
 
 def scan_offsets(counts):

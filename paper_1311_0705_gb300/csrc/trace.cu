@@ -57,6 +57,10 @@ struct TraceArgs {
     uint32_t *stg_start_seg;
     uint32_t *stg_overflow;
     const uint32_t *run_if;  // when non-NULL, the walk runs only if *run_if != 0
+    // interaction points (MODE_INTERACT)
+    const double *tau_int;
+    int32_t *int_cell;
+    double *int_t;
 };
 
 // Stage the first n nodes of the (breadth-first) node list in shared memory.
@@ -493,6 +497,9 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.stg_start_ray = A.stg_start_ray;
     io.stg_start_seg = A.stg_start_seg;
     io.stg_overflow = A.stg_overflow;
+    io.tau_int = A.tau_int;
+    io.int_cell = A.int_cell;
+    io.int_t = A.int_t;
     walk_loop<KIND, MODE, PREC>(src, io, smem, A.n_smem);
 }
 
@@ -502,15 +509,19 @@ typedef void (*KernelFn)(const TraceArgs);
 
 // Walking kernels by [kind][mode][prec][occupancy]; prec runs 0..1, and 0..3
 // for MODE_TAUADJ and MODE_TAUADJ_STAGE (optical depth and gradient precisions).
-constexpr int kModes = 6;
-inline int mode_precs(int m) { return (m == MODE_TAUADJ || m == MODE_TAUADJ_STAGE) ? 4 : 2; }
+constexpr int kModes = 7;
+inline int mode_precs(int m) {
+    return (m == MODE_TAUADJ || m == MODE_TAUADJ_STAGE) ? 4 : (m == MODE_INTERACT ? 1 : 2);
+}
 KernelFn pick_kernel(int kind, int mode, int prec, int occ) {
 #define HG_K(K, M, P) {&trace_kernel<K, M, P, 3>, &trace_kernel<K, M, P, 4>}
 #define HG_M(K, M) {HG_K(K, M, 0), HG_K(K, M, 1), {nullptr, nullptr}, {nullptr, nullptr}}
 #define HG_MA(K, M) {HG_K(K, M, 0), HG_K(K, M, 1), HG_K(K, M, 2), HG_K(K, M, 3)}
+#define HG_M1(K, M) {HG_K(K, M, 0), {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}}
     static const KernelFn table[2][kModes][4][2] = {
-        {HG_M(0, 0), HG_M(0, 1), HG_M(0, 2), HG_MA(0, 3), HG_M(0, 4), HG_MA(0, 5)},
-        {HG_M(1, 0), HG_M(1, 1), HG_M(1, 2), HG_MA(1, 3), HG_M(1, 4), HG_MA(1, 5)}};
+        {HG_M(0, 0), HG_M(0, 1), HG_M(0, 2), HG_MA(0, 3), HG_M(0, 4), HG_MA(0, 5), HG_M1(0, 6)},
+        {HG_M(1, 0), HG_M(1, 1), HG_M(1, 2), HG_MA(1, 3), HG_M(1, 4), HG_MA(1, 5), HG_M1(1, 6)}};
+#undef HG_M1
 #undef HG_MA
 #undef HG_M
 #undef HG_K
@@ -1160,6 +1171,37 @@ extern "C" hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double
     A.status = ray_status;
     A.max_steps = max_steps;
     return launch_trace(g, MODE_TAU, prec, A, block, smem_nodes, schedule, min_blocks, split, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_find_interactions(const hg_grid *g, int64_t n, const double *o, const double *d,
+                                          const double *s_max, double kappa, const double *tau_int,
+                                          const hg_trace_opts *opts, int32_t *cell, double *t, int32_t *ncross,
+                                          uint8_t *ray_status, hg_stream stream) {
+    hg_status st = check_rays(g, n, o, d);
+    if (st != HG_OK) return st;
+    if (n > 0 && (!tau_int || !cell || !t || !ncross)) {
+        set_error("hg_find_interactions: tau_int, cell, t and ncross are required");
+        return HG_EINVAL;
+    }
+    int prec, block, smem_nodes, schedule, min_blocks, split;
+    int64_t max_steps;
+    if ((st = resolve_opts(g, opts, prec, block, smem_nodes, schedule, min_blocks, max_steps, split)) != HG_OK) return st;
+    TraceArgs A{};
+    A.G = g->d;
+    A.n = n;
+    A.o = o;
+    A.d = d;
+    A.smax = s_max;
+    A.kappa = kappa;
+    A.tau_int = tau_int;
+    A.int_cell = cell;
+    A.int_t = t;
+    A.ncross = ncross;
+    A.status = ray_status;
+    A.max_steps = max_steps;
+    // FP64 only, and never cut into segments (where a path stops depends on all that precedes)
+    return launch_trace(g, MODE_INTERACT, HG_FP64, A, block, smem_nodes, schedule, min_blocks, HG_SPLIT_OFF,
+                        (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o, const double *d,

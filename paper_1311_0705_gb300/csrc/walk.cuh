@@ -614,7 +614,17 @@ __device__ __forceinline__ void red_add_keep(double *a, double v, unsigned long 
 // MODE_TAUADJ: the optical depth and the adjoint scatter in one walk.
 // MODE_TAU_STAGE, MODE_TAUADJ_STAGE: the same, also staging every emitted
 // (cell, ds) for a gather into the emission arrays once the counts are known.
-enum { MODE_TAU = 0, MODE_FILL = 1, MODE_ADJ = 2, MODE_TAUADJ = 3, MODE_TAU_STAGE = 4, MODE_TAUADJ_STAGE = 5 };
+// MODE_INTERACT: the walk stops where the accumulated optical depth reaches a
+// drawn tau_int (the interaction point of the Monte Carlo loop).
+enum {
+    MODE_TAU = 0,
+    MODE_FILL = 1,
+    MODE_ADJ = 2,
+    MODE_TAUADJ = 3,
+    MODE_TAU_STAGE = 4,
+    MODE_TAUADJ_STAGE = 5,
+    MODE_INTERACT = 6
+};
 
 // Emission staging: a pool of chunks of kStageChunk entries (cell, ds);
 // each walking thread appends the crossings of the rays and segments it
@@ -639,6 +649,10 @@ struct WalkIO {
     const float *w;
     void *grad;
     const double *rho_ext;  // densities replacing the grid's own (MODE_TAU), or NULL
+    // interaction points (MODE_INTERACT): drawn optical depths in, leaf and path parameter out
+    const double *tau_int = nullptr;
+    int32_t *int_cell = nullptr;
+    double *int_t = nullptr;
     // Path segments: queue items n_rays + s are segment s of a split ray.
     // Each writes its partial results at index s; a combine pass sums them.
     int64_t n_rays = 0x7fffffffffffffffLL;
@@ -674,6 +688,7 @@ template <int KIND, int MODE, int PREC, class Src>
 __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem) {
     constexpr bool SEGS = Src::kSegments;
     constexpr bool STAGE = (MODE == MODE_TAU_STAGE || MODE == MODE_TAUADJ_STAGE);
+    constexpr bool INTER = (MODE == MODE_INTERACT);
     constexpr bool TAU = (MODE == MODE_TAU || MODE == MODE_TAUADJ || STAGE);
     constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_TAUADJ || MODE == MODE_TAUADJ_STAGE);
     constexpr bool TWO = (MODE == MODE_TAUADJ || MODE == MODE_TAUADJ_STAGE);
@@ -694,6 +709,9 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
     uint32_t st = 0;
     bool have = false;
     uint32_t sp = 0;  // staging: next entry position (shifted; 0 = no chunk)
+    double tint = 0.0, it = 0.0;  // interaction: drawn optical depth; interaction time
+    int32_t icell = -1;           // interaction leaf, -1 while none
+    bool walked = false;          // the path has a first leaf (its end time is the current time)
     const float kappa32 = (float)io.kappa;
     const unsigned long long keep = ADJ ? l2_evict_last_policy() : 0ULL;
     for (;;) {
@@ -717,6 +735,17 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             }
             if (MODE == MODE_FILL) seg_base = (SEGS && ray >= io.n_rays) ? io.seg_base[ray - io.n_rays] : io.seg_off[r];
             if (ADJ) wk = io.kappa * (double)io.w[r];
+            if (INTER) {
+                tint = io.tau_int[r];
+                icell = -1;
+                it = 0.0;
+                walked = (rs == WALK_GO);
+                if (((unsigned long long)__double_as_longlong(tint) << 1) > 0xffe0000000000000ULL) {  // NaN
+                    st = HG_RAY_BADINPUT;
+                    walked = false;
+                    rs = WALK_END;
+                }
+            }
             if (rs == WALK_END) goto finish;
             C.id = S.cur;
             C.mode = CAND_ENTER;
@@ -746,10 +775,30 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             double ds, tex;
             bool rec;
             int ax;
+            const long long kin = S.ktcur;  // entry time into this leaf
             const int r = ray_exit<SEGS>(max_steps, S, L, &ds, &rec, &ax, &tex, &st);
             const bool skip = SEGS && (S.sg & SG_SKIP_FIRST) != 0;  // the segment before records this leaf
             if (SEGS) S.sg &= ~SG_SKIP_FIRST;
             if (rec && !skip) {
+                if (INTER) {
+                    // stop in the first segment after which kappa * S reaches tau_int; inside it tau grows
+                    // linearly: t = t_in + (tau_int - kappa S_before) / (kappa rho), at most the exit time
+                    const double rho = L.rho;
+                    const double s_new = acc + rho * ds;
+                    if (io.kappa * s_new >= tint) {
+                        const double a = tint - io.kappa * acc;
+                        const double b = io.kappa * rho;
+                        const double tin = kdouble(kin);
+                        double t = tin;
+                        if (a > 0.0 && b > 0.0) t = tin + a / b;
+                        if (t > tex) t = tex;
+                        icell = S.cur;
+                        it = t;
+                        nc++;
+                        goto finish;
+                    }
+                    acc = s_new;
+                }
                 if (TAU) {
                     if (TPREC == HG_FP64) {
                         const double rho = io.rho_ext ? __ldg(io.rho_ext + S.cur) : L.rho;
@@ -825,6 +874,11 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             }
             io.part_last[sidx] = S.cur;
             io.part_st[sidx] = (uint8_t)st;
+        } else if (INTER) {
+            io.int_cell[ray] = icell;
+            io.int_t[ray] = (icell >= 0) ? it : (walked ? kdouble(S.ktcur) : 0.0);
+            io.ncross[ray] = nc;
+            if (io.status) io.status[ray] = (uint8_t)st;
         } else if (TAU) {
             if (TPREC == HG_FP64)
                 static_cast<double *>(io.tau)[ray] = io.kappa * acc;

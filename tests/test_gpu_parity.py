@@ -494,6 +494,48 @@ def test_taufn_autograd_and_finite_differences(hg, disk_grids):
         assert fd == pytest.approx(g[c], rel=1e-6, abs=1e-10)
 
 
+# ----------------------------------------------------------------------------- interaction points
+
+def _same_interactions(hg, grid, tree, o, k, ti, smax=None, kappa=1.0, **opt):
+    ref = oracle.interact(tree, o, k, ti, smax=smax, kappa=kappa)
+    cell, t, nc, st = hg.find_interactions(grid, _cuda(o), _cuda(k), _cuda(ti), None if smax is None else _cuda(smax),
+                                           kappa=kappa, **opt)
+    np.testing.assert_array_equal(_np(cell), ref["cell"])
+    np.testing.assert_array_equal(_np(nc), ref["ncross"])
+    np.testing.assert_array_equal(_np(st), ref["status"])
+    np.testing.assert_array_equal(_np(t), ref["t"])  # the same FP64 operations in the same order
+    return ref
+
+
+@pytest.mark.parametrize("shape", [dict(), dict(schedule=1), dict(schedule=2, block=128)], ids=["auto", "s1", "s2"])
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_interaction_points_match_oracle(hg, disk_grids, kind, shape):
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    u = np.random.default_rng(31).uniform(size=o.shape[0])
+    ti = -np.log(u) * 0.2  # a mix of interactions and escapes
+    ti[:5] = 0.0
+    ti[5:10] = -1.0
+    ti[10:15] = np.inf
+    ref = _same_interactions(hg, grid, tree, o, k, ti, kappa=1.1, **shape)
+    assert (ref["cell"] >= 0).any() and (ref["cell"] < 0).any()
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_interaction_points_path_ends_and_bad_inputs(hg, disk_grids, kind):
+    model, grids, _, _ = disk_grids
+    grid, tree, _ = grids[kind]
+    a, k, L = synth.endpoint_paths(83, 3001)
+    ti = np.random.default_rng(4).exponential(0.05, 3001)
+    ti[:7] = np.nan
+    _same_interactions(hg, grid, tree, a, k, ti, smax=0.6 * L, kappa=2.0)
+    rng = np.random.default_rng(8)
+    o = rng.uniform(-3, 3, size=(2000, 3))
+    kk = synth.isotropic_dirs(rng, 2000)
+    kk[:10] = 0.0
+    _same_interactions(hg, grid, tree, o, kk, rng.exponential(0.1, 2000))
+
+
 # ----------------------------------------------------------------------------- batching and tuning
 
 def test_batch_matches_single_grid_launches(hg):
