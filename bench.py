@@ -218,7 +218,15 @@ WORKLOADS = {
                   "1e7 rays: FP32-Kahan and FP64 passes plus the adjoint", make_torus_grid),
     "batch-64": ("64 grids (octree/k-d, disk/ring/clumps, seeded), 1e5-1e7 rays each, one persistent launch",
                  None),
+    "interact-1e6": ("disk, octree and k-d tree as disk-1e6; 1e6 photon packets per grid walked to their interaction "
+                     "point (tau_int = -ln u), kappa 200 (face-on tau 12, edge-on ~100 at the centre)",
+                     make_disk_grids),
 }
+# opacity of the interaction workload: the disk optically thick in its midplane
+INTERACT_KAPPA = 200.0
+# interaction search: the walk's bytes per crossing as the FP64 trace; per packet 48 B in, tau_int, then cell,
+# t, count and status out
+INTERACT_BYTES_PER_RAY = 48 + 8 + 4 + 8 + 4 + 1
 
 
 def matched_kd(hg, model, grids, P, PA, PK, PL, RT, TT):
@@ -712,6 +720,120 @@ def _oracle_trees(oracle, grids):
     return trees
 
 
+def run_interact(args):
+    import torch
+    import paper_1311_0705_gb300 as hg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    desc, maker = WORKLOADS[args.workload]
+    model, grids, n_rays, seed = maker(hg)
+    rs = rank_seed(seed, rank)
+    o, k = synth.emission_rays(rs, n_rays)
+    ti = synth.interaction_depths(rs + 5, n_rays)
+    O, K, TI = torch.tensor(o, device=dev), torch.tensor(k, device=dev), torch.tensor(ti, device=dev)
+    for g in grids:
+        g["grid"] = hg.load_grid(g["host"], validate=args.validate)
+        g["out"] = (torch.empty(n_rays, dtype=torch.int32, device=dev), torch.empty(n_rays, dtype=torch.float64,
+                                                                                 device=dev),
+                    torch.empty(n_rays, dtype=torch.int32, device=dev), torch.empty(n_rays, dtype=torch.uint8,
+                                                                                 device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    kev = {g["name"]: [] for g in grids}
+
+    def step(record=False):
+        for g in grids:
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            hg.find_interactions(g["grid"], O, K, TI, kappa=INTERACT_KAPPA, out=g["out"])
+            if record:
+                e1.record(stream)
+                kev[g["name"]].append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for g in grids:
+        bits = int(hg.reduce_status(g["out"][3]).item())
+        if bits:
+            raise RuntimeError(f"ray status bits {bits} on {g['name']}")
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = hg.launch_count()
+    barrier(dist, dev)
+    torch.cuda.synchronize()
+    times = _timed_steps(torch, stream, args.steps, flush, lambda: step(True))
+    barrier(dist, dev)
+    launches = hg.launch_count() - l0
+    clk = clocks.stop()
+    tot_ms = max_over_ranks(dist, sum(times), dev)
+    value = sum_over_ranks(dist, n_rays * len(grids) * args.steps, dev) / (tot_ms / 1e3)
+    peak, src = _peak()
+    kern, tb, tt = {}, 0.0, 0.0
+    for g in grids:
+        cell, t, nc, st = g["out"]
+        cr = int(nc.sum().item())
+        ms = statistics.mean(a.elapsed_time(b) for a, b in kev[g["name"]])
+        byt = BYTES_PER_CROSSING["fp64"] * cr + INTERACT_BYTES_PER_RAY * n_rays
+        kern[g["name"]] = dict(leaves=g["grid"].n_leaves, walk_ms=ms, packets_per_s=n_rays / ms * 1e3,
+                               mean_ncross=cr / n_rays, gcross_per_s=cr / ms / 1e6,
+                               interacted=float((cell >= 0).float().mean().item()), algorithmic_bytes=byt)
+        tb += byt
+        tt += ms
+    ach = tb / (tt / 1e3) / 1e9
+    roofline = dict(bound="hbm", achieved=round(ach, 1), peak=peak, unit="GB/s", frac=round(ach / peak, 4),
+                    traffic=None, kernel="trace_kernel interaction search (hg_find_interactions)", peak_source=src)
+    e2e = None
+    if not args.no_e2e:
+        ho, hk, hti = torch.tensor(o).pin_memory(), torch.tensor(k).pin_memory(), torch.tensor(ti).pin_memory()
+        hc = [torch.empty(n_rays, dtype=torch.int32).pin_memory() for _ in grids]
+        ht = [torch.empty(n_rays, dtype=torch.float64).pin_memory() for _ in grids]
+
+        def e2e_step():
+            O.copy_(ho, non_blocking=True)
+            K.copy_(hk, non_blocking=True)
+            TI.copy_(hti, non_blocking=True)
+            step()
+            for j, g in enumerate(grids):
+                hc[j].copy_(g["out"][0], non_blocking=True)
+                ht[j].copy_(g["out"][1], non_blocking=True)
+
+        barrier(dist, dev)
+        et = _timed_steps(torch, stream, args.steps, flush, e2e_step)
+        barrier(dist, dev)
+        e_ms = max_over_ranks(dist, sum(et), dev)
+        e2e = dict(value=sum_over_ranks(dist, n_rays * len(grids) * args.steps, dev) / (e_ms / 1e3), unit=UNIT,
+                   h2d_bytes_per_step=n_rays * (24 + 24 + 8), d2h_bytes_per_step=len(grids) * n_rays * (4 + 8))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        trees = _oracle_trees(oracle, grids)
+        threads = os.cpu_count() or 1
+        n = min(args.cpu_sample, n_rays)
+        t0 = time.perf_counter()
+        for T in trees:
+            oracle.interact(T, o[:n], k[:n], ti[:n], kappa=INTERACT_KAPPA, threads=threads)
+        dt = time.perf_counter() - t0
+        cpu = dict(value=n * len(trees) / dt, unit=UNIT, cores=threads, kind="oracle",
+                   sample=f"{n} of the {n_rays} packets per grid through {len(trees)} grids: interaction search")
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=tot_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, description=desc, packets_per_grid=n_rays, kappa=INTERACT_KAPPA,
+                            grids=kern,
+                            l2="flushed between steps (512 MB write)"),
+                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(model, grids, o, k, pts, pa, pk, pl, w, sample: int = 200_000):
     import oracle
     threads = os.cpu_count() or 1
@@ -790,6 +912,8 @@ def main(argv=None):
         run_torus(args)
     elif args.workload == "batch-64":
         run_batch(args)
+    elif args.workload == "interact-1e6":
+        run_interact(args)
     else:
         run_ours(args)
 

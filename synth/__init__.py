@@ -221,6 +221,14 @@ def endpoint_paths(seed: int, n: int, lo=-1.0, hi=1.0):
     return np.ascontiguousarray(a), np.ascontiguousarray(v / L[:, None]), np.ascontiguousarray(L)
 
 
+def interaction_depths(seed: int, n: int) -> np.ndarray:
+    """Optical depths to the next interaction of photon packets, tau = -ln u with u uniform in (0, 1]
+    (the draw of the Monte Carlo loop; passed to both sides as an input)."""
+    rng = np.random.default_rng(seed)
+    u = 1.0 - rng.random(n)  # (0, 1]
+    return np.ascontiguousarray(-np.log(u))
+
+
 def sample_points(seed: int, n: int, lo=-1.0, hi=1.0) -> np.ndarray:
     lo, hi = _box(lo, hi)
     rng = np.random.default_rng(seed)
