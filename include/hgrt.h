@@ -138,6 +138,13 @@ typedef struct hg_host_grid hg_host_grid;
  * Deterministic: the result does not depend on n_threads. */
 hg_status hg_build_grid(const hg_model *model, const hg_build_params *params, int32_t n_threads,
                         hg_host_grid **out);
+/* The tau_max recipe of Sect. 4.1: build with params' mass criterion only
+ * (use_tau and use_q ignored), sort the leaves' optical depths (Eq. 2) in
+ * ascending order and return in *tau_max the one at 0-based position
+ * floor(fraction * N_leaves) (at most N_leaves - 1); the paper takes
+ * fraction = 0.9.  Build then with the mass criterion and this tau_max. */
+hg_status hg_tau_max_recipe(const hg_model *model, const hg_build_params *params, double fraction,
+                            int32_t n_threads, double *tau_max);
 /* View the built grid as a description (pointers stay valid until hg_free_host_grid). */
 hg_status hg_host_grid_desc(const hg_host_grid *g, hg_grid_desc *out);
 hg_status hg_host_grid_nodes(const hg_host_grid *g, hg_host_nodes *out);

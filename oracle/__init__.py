@@ -12,6 +12,8 @@ from __future__ import annotations
 
 import concurrent.futures as _cf
 import ctypes as C
+import dataclasses
+import math
 import os
 import subprocess
 import threading
@@ -252,6 +254,16 @@ def build_tree(model, bp, max_nodes: int = 0) -> Tree:
     if rc != 0:
         raise RuntimeError(f"oracle build failed ({rc})")
     return _export(h, int(bp.kind))
+
+
+def tau_max_recipe(model, bp, fraction: float = 0.9) -> float:
+    """The tau_max recipe of Sect. 4.1 in the oracle: build with the mass criterion only, sort the
+    leaves' optical depths (Eq. 2) ascending, take the one at 0-based position floor(fraction * N)."""
+    b = dataclasses.replace(bp, use_tau=False, use_q=False)
+    t = build_tree(model, b)
+    taus = np.sort(t.taun[t.child < 0])
+    n = taus.shape[0]
+    return float(taus[min(int(math.floor(fraction * n)), n - 1)])
 
 
 def wrap_tree(kind: int, node_lo, node_hi, child, leaf, leaf_rho) -> Tree:

@@ -94,6 +94,8 @@ _I64 = C.c_int64
 _S = C.c_int  # hg_status
 _SIGS = {
     "hg_build_grid": (_S, [C.POINTER(_Model), C.POINTER(_BuildParams), C.c_int32, C.POINTER(_V)]),
+    "hg_tau_max_recipe": (_S, [C.POINTER(_Model), C.POINTER(_BuildParams), C.c_double, C.c_int32,
+                               C.POINTER(C.c_double)]),
     "hg_host_grid_desc": (_S, [_V, C.POINTER(_Desc)]),
     "hg_host_grid_nodes": (_S, [_V, C.POINTER(_HostNodes)]),
     "hg_free_host_grid": (None, [_V]),
@@ -265,9 +267,7 @@ class HostGrid:
             self._h = None
 
 
-def build_grid(model, params, threads: int = 0) -> HostGrid:
-    """Host tree construction (hg_build_grid): node list, criteria of Eq. 1-3, neighbor lists."""
-    m, _keep = _model_struct(model)
+def _build_params(params):
     p = _BuildParams()
     p.kind = int(params.kind)
     p.use_delta = int(bool(params.use_delta))
@@ -281,9 +281,27 @@ def build_grid(model, params, threads: int = 0) -> HostGrid:
     p.n_ran = int(params.n_ran)
     p.seed = int(params.seed) & ((1 << 64) - 1)
     p.max_nodes = int(getattr(params, "max_nodes", 0) or 0)
+    return p
+
+
+def build_grid(model, params, threads: int = 0) -> HostGrid:
+    """Host tree construction (hg_build_grid): node list, criteria of Eq. 1-3, neighbor lists."""
+    m, _keep = _model_struct(model)
+    p = _build_params(params)
     h = C.c_void_p()
     _check(_lib.hg_build_grid(C.byref(m), C.byref(p), int(threads), C.byref(h)), "hg_build_grid")
     return HostGrid(h)
+
+
+def tau_max_recipe(model, params, fraction: float = 0.9, threads: int = 0) -> float:
+    """The tau_max recipe of Sect. 4.1 (hg_tau_max_recipe): the leaf optical depth at position
+    floor(fraction * N) of the sorted list of a grid built with the mass criterion only."""
+    m, _keep = _model_struct(model)
+    p = _build_params(params)
+    out = C.c_double()
+    _check(_lib.hg_tau_max_recipe(C.byref(m), C.byref(p), float(fraction), int(threads), C.byref(out)),
+           "hg_tau_max_recipe")
+    return float(out.value)
 
 
 @dataclass

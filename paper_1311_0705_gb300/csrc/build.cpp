@@ -411,6 +411,39 @@ extern "C" hg_status hg_build_grid(const hg_model *model, const hg_build_params 
     return HG_OK;
 }
 
+// The tau_max recipe of Sect. 4.1: build with the mass criterion only, sort
+// the leaves' optical depths (Eq. 2, as the builder computes them) in
+// ascending order and take the one at position floor(fraction * N_leaves)
+// (0-based, at most N_leaves - 1); the paper uses fraction 0.9.
+extern "C" hg_status hg_tau_max_recipe(const hg_model *model, const hg_build_params *params, double fraction,
+                                       int32_t n_threads, double *tau_max) {
+    if (!params || !tau_max || !(fraction >= 0.0 && fraction <= 1.0)) {
+        hg::set_error("hg_tau_max_recipe: bad arguments (fraction must lie in [0, 1])");
+        return HG_EINVAL;
+    }
+    hg_build_params p = *params;
+    p.use_tau = 0;
+    p.use_q = 0;
+    hg_host_grid *G = nullptr;
+    hg_status st = hg_build_grid(model, &p, n_threads, &G);
+    if (st != HG_OK) return st;
+    try {
+        std::vector<double> t;
+        t.reserve(G->leaf_node.size());
+        for (const int64_t nd : G->leaf_node) t.push_back(G->tau[nd]);
+        std::sort(t.begin(), t.end());
+        const int64_t N = (int64_t)t.size();
+        const int64_t i = std::min<int64_t>((int64_t)std::floor(fraction * (double)N), N - 1);
+        *tau_max = t[(size_t)i];
+    } catch (const std::bad_alloc &) {
+        delete G;
+        hg::set_error("hg_tau_max_recipe: out of host memory");
+        return HG_ENOMEM;
+    }
+    delete G;
+    return HG_OK;
+}
+
 extern "C" hg_status hg_host_grid_desc(const hg_host_grid *g, hg_grid_desc *out) {
     if (!g || !out) { hg::set_error("hg_host_grid_desc: null argument"); return HG_EINVAL; }
     out->kind = g->kind;

@@ -182,3 +182,21 @@ def test_single_leaf_grid_has_no_neighbor_entries():
     bp = synth.BuildParams(kind=0, delta_max=2.0, max_level=4)
     H = hg.build_grid(synth.make_const(1.0), bp)
     assert H.n_leaves == 1 and H.nbr_id.size == 0 and (H.nbr_off == 0).all()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_tau_max_recipe_matches_oracle(kind):
+    # Sect. 4.1: tau_max = the leaf optical depth at position floor(0.9 N) of a mass-criterion-only grid
+    model = synth.make_torus(13, n_clumps=40)
+    bp = synth.BuildParams(kind=kind, delta_max=2e-3, use_tau=True, tau_max=123.0, use_q=True, max_level=5)
+    for frac in (0.9, 0.5, 1.0, 0.0):
+        got = hg.tau_max_recipe(model, bp, fraction=frac, threads=3)
+        assert got == oracle.tau_max_recipe(model, bp, fraction=frac)
+    tm = hg.tau_max_recipe(model, bp)
+    H = hg.build_grid(model, synth.BuildParams(kind=kind, delta_max=2e-3, max_level=5))
+    taus = H.tau[H.leaf_node]
+    # at most 10 % of the leaves lie above it, and only ties keep the count below 10 % - 1
+    above = int((taus > tm).sum())
+    assert above <= int(0.1 * H.n_leaves) + 1 and (taus >= tm).sum() >= H.n_leaves - int(0.9 * H.n_leaves)
+    with pytest.raises(hg.HgError):
+        hg.tau_max_recipe(model, bp, fraction=1.5)
