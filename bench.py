@@ -786,7 +786,8 @@ def run_interact(args):
         tt += ms
     ach = tb / (tt / 1e3) / 1e9
     roofline = dict(bound="hbm", achieved=round(ach, 1), peak=peak, unit="GB/s", frac=round(ach / peak, 4),
-                    traffic=None, kernel="trace_kernel interaction search (hg_find_interactions)", peak_source=src)
+                    traffic=recorded_traffic(args.workload, "fp64"),
+                    kernel="trace_kernel interaction search (hg_find_interactions)", peak_source=src)
     e2e = None
     if not args.no_e2e:
         ho, hk, hti = torch.tensor(o).pin_memory(), torch.tensor(k).pin_memory(), torch.tensor(ti).pin_memory()
