@@ -47,10 +47,7 @@ UNIT = "rays/s"
 # wall's CSR range (2 x int64) + one neighbor id; per ray origin + direction in, tau + count + status out
 BYTES_PER_CROSSING = {"fp64": 48 + 8 + 16 + 4, "fp32k": 48 + 4 + 16 + 4}
 BYTES_PER_RAY = {"fp64": 48 + 8 + 4 + 1, "fp32k": 48 + 4 + 4 + 1}
-# fused into the same walk: the adjoint scatter (an FP32 gradient read-modify-write per crossing, w per
-# ray) and the emission staging (cell and ds per crossing, the first entry per ray)
-ADJ_BYTES_PER_CROSSING = 4 + 4
-ADJ_BYTES_PER_RAY = 4
+# fused into the same walk: the emission staging (cell and ds per crossing, the first entry per ray)
 STAGE_BYTES_PER_CROSSING = {"fp64": 4 + 8, "fp32k": 4 + 4}
 STAGE_BYTES_PER_RAY = 4
 L2_FLUSH_BYTES = 512 << 20
@@ -305,20 +302,21 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     kev = []  # (start, end) events around the dominant kernel
+    cev = []  # (start, end) events around the emission copy with the adjoint scatter
 
     def step(record=False):
         out = {}
         for g in grids:
             G = g["grid"]
             # one setup (first leaf, work-ordered queue, path segments) for these rays; one walk for
-            # the optical depth, counts, adjoint and the staged emission; then the emission copy
+            # the optical depth, counts and the staged emission; then the emission copy, which also
+            # scatters the adjoint from the staged lengths
             R = hg.prepare_rays(G, O, K)
             g["grad"].zero_()
             if record:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            R.trace_stage(kappa=1.0, precision=prec, w=W, grad=g["grad"], grad_precision="fp32",
-                          out=(g["tau"], g["nc"], g["st"]))
+            R.trace_stage(kappa=1.0, precision=prec, out=(g["tau"], g["nc"], g["st"]))
             if record:
                 e1.record(stream)
                 kev.append((g["name"], e0, e1))
@@ -327,7 +325,14 @@ def run_ours(args):
             cap = g.get("cap")
             if cap is None:
                 cap = g["cap"] = int(off[-1].item())
-            cell, ds = R.emit_staged(off, capacity=cap, status=g["st"])
+            if record:
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+            cell, ds, _ = R.emit_staged_gradient(off, W, kappa=1.0, grad=g["grad"], grad_precision="fp32",
+                                                 capacity=cap, status=g["st"])
+            if record:
+                c1.record(stream)
+                cev.append((g["name"], c0, c1))
             _, rg = hg.sample_density(G, P)
             drho = hg.diff_stats(RT, rg)
             ptau, _, _ = hg.trace_rays(G, PA, PK, PL, kappa=1.0, precision="fp64", out=(g["ptau"], g["pnc"], None))
@@ -370,20 +375,23 @@ def run_ours(args):
     all_rays = sum_over_ranks(dist, rays_per_step * args.steps, dev)
     value = all_rays / (tot_ms / 1e3)
 
-    # dominant kernel: the walk for optical depth, adjoint and staged emission; algorithmic bytes per launch /
+    # dominant kernel: the walk for optical depth and staged emission; algorithmic bytes per launch /
     # mean launch time
-    per = {}
+    per, cper = {}, {}
     for name, e0, e1 in kev:
         per.setdefault(name, []).append(e0.elapsed_time(e1))
+    for name, e0, e1 in cev:
+        cper.setdefault(name, []).append(e0.elapsed_time(e1))
     kern = {}
     tot_bytes, tot_time = 0.0, 0.0
     for g in grids:
         cr = int(g["nc"].sum().item())
         ms = statistics.mean(per[g["name"]])
-        byt = ((BYTES_PER_CROSSING[prec] + ADJ_BYTES_PER_CROSSING + STAGE_BYTES_PER_CROSSING[prec]) * cr +
-               (BYTES_PER_RAY[prec] + ADJ_BYTES_PER_RAY + STAGE_BYTES_PER_RAY) * n_rays)
+        byt = ((BYTES_PER_CROSSING[prec] + STAGE_BYTES_PER_CROSSING[prec]) * cr +
+               (BYTES_PER_RAY[prec] + STAGE_BYTES_PER_RAY) * n_rays)
         kern[g["name"]] = dict(leaves=g["grid"].n_leaves, build_s=round(g["build_s"], 2), load_s=round(g["load_s"], 2),
                                mean_ncross=cr / n_rays, trace_ms=ms, trace_rays_per_s=n_rays / ms * 1e3,
+                               copy_adjoint_ms=statistics.mean(cper[g["name"]]),
                                gcross_per_s=cr / ms / 1e6, algorithmic_bytes=byt,
                                delta_rho=float(results[g["name"]][1][2].item()),
                                delta_tau=float(results[g["name"]][2][2].item()))
@@ -398,8 +406,8 @@ def run_ours(args):
     achieved = tot_bytes / (tot_time / 1e3) / 1e9
     traffic = recorded_traffic(args.workload, prec)
     roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s", frac=round(achieved / peak, 4),
-                    traffic=traffic, kernel="trace_kernel, one walk for optical depth, adjoint and staged "
-                                            "emission over prepared rays (hg_rays_trace_stage)",
+                    traffic=traffic, kernel="trace_kernel, one walk for optical depth and staged emission over "
+                                            "prepared rays (hg_rays_trace_stage)",
                     peak_source="measured" if "hbm_gbs" in peaks else "fallback")
 
     # e2e: the same step through the public API with host buffers (pinned), copies inside the timed region

@@ -352,6 +352,20 @@ hg_status hg_rays_trace_stage(hg_rays *r, double kappa, const double *rho, int32
                               void *grad_rho, int32_t stage_per_ray, hg_stream stream);
 hg_status hg_rays_emit_staged(hg_rays *r, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
                               int64_t seg_capacity, uint8_t *ray_status, hg_stream stream);
+/* hg_rays_emit_staged that also accumulates the adjoint of the optical depth
+ * (for L = sum_i w_i tau_i, as hg_tau_gradient): grad_rho[c] += kappa w_i ds
+ * for every staged crossing of ray i through leaf c -- what hg_rays_gradient
+ * adds, taken from the staged lengths in the same pass as the copy instead
+ * of a walk (ds as staged: FP32 after an HG_FP32K trace).  Meant after
+ * hg_rays_trace_stage with w NULL (with w, the walk has already added the
+ * gradient once).  grad_precision 0:
+ * grad_rho is double[n_leaves], 1: float[n_leaves]; w is float[n] of device
+ * memory; the gradient does not depend on seg_capacity.  When the pool
+ * overflowed, a fill walk and a gradient walk do the work instead.  The
+ * order of the atomic additions is unspecified. */
+hg_status hg_rays_emit_staged_gradient(hg_rays *r, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
+                                       int64_t seg_capacity, uint8_t *ray_status, double kappa, const float *w,
+                                       int32_t grad_precision, void *grad_rho, hg_stream stream);
 /* As hg_trace_fill; seg_off from hg_scan_offsets over the ncross of
  * hg_rays_trace (or hg_rays_trace_gradient) on the same rays. */
 hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,

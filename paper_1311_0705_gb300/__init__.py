@@ -116,6 +116,7 @@ _SIGS = {
     "hg_rays_trace_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V, C.c_int32, _V, _V]),
     "hg_rays_trace_stage": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V, _V, _V, C.c_int32, _V, C.c_int32, _V]),
     "hg_rays_emit_staged": (_S, [_V, _V, _V, _V, _I64, _V, _V]),
+    "hg_rays_emit_staged_gradient": (_S, [_V, _V, _V, _V, _I64, _V, C.c_double, _V, C.c_int32, _V, _V]),
     "hg_rays_fill": (_S, [_V, C.c_int32, _V, _V, _V, _I64, _V, _V]),
     "hg_rays_gradient": (_S, [_V, C.c_double, _V, C.c_int32, _V, _V]),
     "hg_rays_free": (None, [_V, _V]),
@@ -635,14 +636,46 @@ class Rays:
                "hg_rays_emit_staged")
         return cell[:capacity], ds[:capacity]
 
+    def emit_staged_gradient(self, seg_off, w, kappa: float = 1.0, grad=None, grad_precision="fp32",
+                             capacity: Optional[int] = None, status=None, out=None):
+        """hg_rays_emit_staged_gradient: the staged emission copied to its CSR slots while the adjoint
+        (kappa w ds per staged crossing) accumulates into grad.  Returns (cell, ds, grad)."""
+        torch = _torch()
+        n = self.n
+        ddt = torch.float64 if getattr(self, "_stage_prec", FP64) == FP64 else torch.float32
+        gp = {"fp64": 0, "fp32": 1}[grad_precision]
+        gdt = torch.float64 if gp == 0 else torch.float32
+        if capacity is None:
+            capacity = int(seg_off[-1].item())
+        if out is None:
+            cell = torch.empty(max(capacity, 1), dtype=torch.int32, device=self.device)
+            ds = torch.empty(max(capacity, 1), dtype=ddt, device=self.device)
+        else:
+            cell, ds = out
+        if grad is None:
+            grad = torch.zeros(self.grid.n_leaves, dtype=gdt, device=self.device)
+        _check(_lib.hg_rays_emit_staged_gradient(
+            self._h, _dptr(seg_off, torch.int64, (n + 1,)), _dptr(cell), _dptr(ds, ddt), int(capacity),
+            _dptr(status, torch.uint8, (n,), "status"), float(kappa), _dptr(w, torch.float32, (n,), "w"), gp,
+            _dptr(grad, gdt, (self.grid.n_leaves,), "grad"), _stream()), "hg_rays_emit_staged_gradient")
+        return cell[:capacity], ds[:capacity], grad
+
     def emit_single_pass(self, kappa: float = 1.0, precision="fp64", w=None, grad=None, grad_precision="fp32",
-                         stage_per_ray: int = 0):
+                         stage_per_ray: int = 0, adjoint: str = "copy"):
         """Optical depth (and gradient) with the emission in one walk plus a copy:
-        tau, ncross, status, seg_off, seg_cell, seg_ds (and grad)."""
-        tau, nc, st, g = self.trace_stage(kappa, precision, w=w, grad=grad, grad_precision=grad_precision,
-                                          stage_per_ray=stage_per_ray)
+        tau, ncross, status, seg_off, seg_cell, seg_ds (and grad).  With w, adjoint="copy" scatters
+        the gradient from the staged lengths during the copy; "walk" scatters it inside the walk."""
+        if adjoint not in ("copy", "walk"):
+            raise ValueError("adjoint must be 'copy' or 'walk'")
+        in_walk = w is not None and adjoint == "walk"
+        tau, nc, st, g = self.trace_stage(kappa, precision, w=w if in_walk else None, grad=grad,
+                                          grad_precision=grad_precision, stage_per_ray=stage_per_ray)
         off = scan_offsets(nc)
-        cell, ds = self.emit_staged(off, status=st)
+        if w is None or in_walk:
+            cell, ds = self.emit_staged(off, status=st)
+        else:
+            cell, ds, g = self.emit_staged_gradient(off, w, kappa=kappa, grad=grad, grad_precision=grad_precision,
+                                                    status=st)
         return dict(tau=tau, ncross=nc, status=st, seg_off=off, seg_cell=cell, seg_ds=ds, grad=g)
 
     def fill(self, seg_off, precision="fp64", capacity: Optional[int] = None, status=None, out=None):

@@ -31,6 +31,7 @@ struct TraceArgs {
     int64_t seg_cap;
     const float *w;
     void *grad;
+    uint32_t gmul, gmask;   // gradient slot of leaf c: (c * gmul) & gmask; gmul 0: slot c
     const double *rho_ext;  // densities replacing the grid's own (MODE_TAU), or NULL
     int64_t max_steps;
     unsigned long long *counter;
@@ -481,6 +482,10 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.seg_cap = A.seg_cap;
     io.w = A.w;
     io.grad = A.grad;
+    if (A.gmul) {
+        io.gmul = A.gmul;
+        io.gmask = A.gmask;
+    }
     io.rho_ext = A.rho_ext;
     io.n_rays = A.n;
     io.segs = A.segs;
@@ -652,6 +657,10 @@ struct hg_rays {
     unsigned long long *stg_ctr = nullptr;
     uint32_t stg_nchunks = 0;
     int stg_prec = -1;    // precision of the staged lengths; -1: nothing staged
+    // gradient scratch: 2^k slots >= n_leaves, leaf c accumulated at slot (c * gscr_mul) & gscr_mask
+    void *gscr = nullptr;
+    size_t gscr_bytes = 0;
+    uint32_t gscr_mul = 0, gscr_mask = 0;
 };
 
 namespace hg {
@@ -769,6 +778,65 @@ void free_plan(hg_rays &P, cudaStream_t stream) {
     if (P.stg) cudaFreeAsync(P.stg, stream);
     P.stg = nullptr;
     P.stg_bytes = 0;
+    if (P.gscr) cudaFreeAsync(P.gscr, stream);
+    P.gscr = nullptr;
+    P.gscr_bytes = 0;
+}
+
+// The gradient walks and the copy of a plan scatter into a zeroed scratch
+// of 2^k slots (2^k >= n_leaves), leaf c at slot (c * mul) mod 2^k with mul
+// odd near 0.618 * 2^k: a bijection that puts consecutive leaf ids (which
+// the builder gives to spatially close leaves) about 0.618 * 2^k slots
+// apart.  Rays crossing a dense region then spread their atomic adds over
+// many L2 lines instead of queueing on the few that hold its leaves.
+// grad_scratch_begin allocates and zeroes it and points A at it;
+// grad_scratch_end adds slot (c * mul) mod 2^k to grad[c] for every leaf.
+hg_status grad_scratch_begin(hg_rays &P, int gp, TraceArgs &A, cudaStream_t stream) {
+    const int64_t nl = std::max<int64_t>(P.g->d.n_leaves, 1);
+    int k = 0;
+    while (((int64_t)1 << k) < nl) k++;
+    const size_t bytes = ((size_t)1 << k) * (gp == 0 ? sizeof(double) : sizeof(float));
+    if (bytes > P.gscr_bytes) {
+        if (P.gscr) cudaFreeAsync(P.gscr, stream);
+        P.gscr = nullptr;
+        P.gscr_bytes = 0;
+        cudaError_t e = cudaMallocAsync(&P.gscr, bytes, stream);
+        if (e != cudaSuccess) {
+            P.gscr = nullptr;
+            return cuda_err(e, "gradient scratch");
+        }
+        P.gscr_bytes = bytes;
+    }
+    cudaError_t e = cudaMemsetAsync(P.gscr, 0, bytes, stream);
+    if (e != cudaSuccess) return cuda_err(e, "gradient scratch reset");
+    P.gscr_mask = (uint32_t)(((uint64_t)1 << k) - 1);
+    P.gscr_mul = (uint32_t)(0.6180339887498949 * (double)((uint64_t)1 << k)) | 1u;
+    A.grad = P.gscr;
+    A.gmul = P.gscr_mul;
+    A.gmask = P.gscr_mask;
+    return HG_OK;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) grad_unhash_kernel(int64_t n, const T *__restrict__ scr, uint32_t mul,
+                                                          uint32_t mask, T *grad) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        grad[c] += scr[((uint32_t)c * mul) & mask];
+}
+
+hg_status grad_scratch_end(hg_rays &P, int gp, void *grad, cudaStream_t stream) {
+    const int64_t n = P.g->d.n_leaves;
+    if (n <= 0) return HG_OK;
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    if (gp == 0)
+        grad_unhash_kernel<double><<<blocks, 256, 0, stream>>>(n, static_cast<const double *>(P.gscr), P.gscr_mul,
+                                                              P.gscr_mask, static_cast<double *>(grad));
+    else
+        grad_unhash_kernel<float><<<blocks, 256, 0, stream>>>(n, static_cast<const float *>(P.gscr), P.gscr_mul,
+                                                             P.gscr_mask, static_cast<float *>(grad));
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HG_OK : cuda_err(e, "gradient unhash");
 }
 
 // Size the staging pool: per_ray entries per ray plus one chunk per walking
@@ -820,20 +888,32 @@ hg_status make_staging(hg_rays &P, int prec, int64_t per_ray, cudaStream_t strea
 // g of the group, G a power of two dividing 32): each chunk piece is read
 // and written by consecutive lanes.  Entries at or beyond cap are dropped
 // (returns false then, on every lane of the group).
-template <int G, typename DS>
+// GP >= 0: also scatter the adjoint, grad[slot(cell)] += wk * ds (wk = kappa
+// w of the ray; GP 0 FP64, 1 FP32 gradient; slot(c) = (c * gmul) & gmask),
+// for every entry, dropped or not.
+template <int G, int GP, typename DS>
 __device__ __forceinline__ bool copy_staged_group(uint32_t e, int64_t cnt, int64_t b,
                                                   const int32_t *__restrict__ cell, const DS *__restrict__ ds,
                                                   const uint32_t *__restrict__ next, int32_t *out_cell, DS *out_ds,
-                                                  int64_t cap, int g) {
+                                                  int64_t cap, int g, double wk, void *grad, uint32_t gmul,
+                                                  uint32_t gmask, unsigned long long keep) {
     bool fit = true;
     while (cnt > 0) {
         const int64_t piece = std::min<int64_t>(cnt, (int64_t)(kStageChunk - (e & (kStageChunk - 1u))));
         for (int64_t k = g; k < piece; k += G) {
+            const int32_t c = cell[e + k];
+            const DS l = ds[e + k];
             if (b + k < cap) {
-                out_cell[b + k] = cell[e + k];
-                out_ds[b + k] = ds[e + k];
+                out_cell[b + k] = c;
+                out_ds[b + k] = l;
             } else {
                 fit = false;
+            }
+            const uint32_t slot = ((uint32_t)c * gmul) & gmask;
+            if (GP == 0) {
+                red_add_keep(static_cast<double *>(grad) + slot, wk * (double)l, keep);
+            } else if (GP == 1) {
+                red_add_keep(static_cast<float *>(grad) + slot, __double2float_rn(wk * (double)l), keep);
             }
         }
         cnt -= piece;
@@ -844,10 +924,12 @@ __device__ __forceinline__ bool copy_staged_group(uint32_t e, int64_t cnt, int64
 }
 
 // Emission from the staging pool: each ray's crossings (or its segments',
-// in path order with the counts of the staged walk) copied to its CSR slot
-// by one warp.  Does nothing when the pool overflowed (the fill walk that
-// follows then does the emission).
-template <typename DS>
+// in path order with the counts of the staged walk) copied to its CSR slot,
+// eight lanes per unsplit ray and a warp per split ray; with GP >= 0 the
+// same pass scatters the adjoint (kappa w of the ray times each length).
+// Does nothing when the pool overflowed (the walks that follow then do the
+// emission and the adjoint).
+template <int GP, typename DS>
 __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *__restrict__ starts,
                                                      const int64_t *__restrict__ seg_off,
                                                      const uint32_t *__restrict__ start_ray,
@@ -857,19 +939,25 @@ __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *
                                                      const int32_t *__restrict__ part_nc,
                                                      const int32_t *__restrict__ cell, const DS *__restrict__ ds,
                                                      const uint32_t *__restrict__ next, const uint32_t *overflow,
-                                                     int32_t *out_cell, DS *out_ds, int64_t cap, uint8_t *status) {
+                                                     int32_t *out_cell, DS *out_ds, int64_t cap, uint8_t *status,
+                                                     double kappa, const float *__restrict__ w, void *grad,
+                                                     uint32_t gmul, uint32_t gmask) {
     if (*overflow) return;
+    const unsigned long long keep = GP >= 0 ? l2_evict_last_policy() : 0ULL;
     constexpr int G = 8;  // lanes per unsplit ray: four rays per warp in flight
     const int lane = threadIdx.x & 31, g = lane & (G - 1);
-    const unsigned gmask = 0xffu << (lane & ~(G - 1));
+    const unsigned lanes = 0xffu << (lane & ~(G - 1));
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x / G);
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     for (int64_t r = g0; r < n; r += ngroups) {
         if (starts[r].sg & SG_SPLIT) continue;
         const int64_t b = seg_off[r], cnt = seg_off[r + 1] - b;
         if (cnt <= 0) continue;
-        const bool fit = copy_staged_group<G>(start_ray[r], cnt, b, cell, ds, next, out_cell, out_ds, cap, g);
-        if (!__all_sync(gmask, fit) && status && g == 0) status[r] |= HG_RAY_OVERFLOW;
+        const double wk = GP >= 0 ? kappa * (double)__ldg(w + r) : 0.0;
+        const bool fit =
+            copy_staged_group<G, GP>(start_ray[r], cnt, b, cell, ds, next, out_cell, out_ds, cap, g, wk, grad, gmul,
+                                     gmask, keep);
+        if (!__all_sync(lanes, fit) && status && g == 0) status[r] |= HG_RAY_OVERFLOW;
     }
     // split rays: one warp each, segments in path order
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -878,12 +966,13 @@ __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *
     for (int64_t i = w0; i < m; i += nw) {
         const SplitRec rec = list[i];
         int64_t b = seg_off[rec.ray];
+        const double wk = GP >= 0 ? kappa * (double)__ldg(w + rec.ray) : 0.0;
         bool fit = true;
         for (int j = 0; j < rec.count; j++) {
             const int64_t cnt = part_nc[rec.first + j];
             if (cnt > 0)
-                fit = copy_staged_group<32>(start_seg[rec.first + j], cnt, b, cell, ds, next, out_cell, out_ds, cap,
-                                            lane) &&
+                fit = copy_staged_group<32, GP>(start_seg[rec.first + j], cnt, b, cell, ds, next, out_cell, out_ds,
+                                                cap, lane, wk, grad, gmul, gmask, keep) &&
                       fit;
             b += cnt;
         }
@@ -979,7 +1068,14 @@ hg_status launch_trace(const hg_grid *g, int mode, int prec, TraceArgs A, int bl
     hg_status hs = make_plan(P, g, A.n, A.o, A.d, A.smax, block, smem_nodes, schedule, min_blocks, A.max_steps,
                              mode == MODE_TAU || mode == MODE_ADJ, split, mode == MODE_FILL ? A.seg_off : nullptr,
                              stream);
-    if (hs == HG_OK) hs = walk_plan(P, mode, prec, A, stream);
+    if (mode == MODE_ADJ) {  // through the hashed gradient slots (prec: the gradient's precision)
+        void *grad = A.grad;
+        if (hs == HG_OK) hs = grad_scratch_begin(P, prec, A, stream);
+        if (hs == HG_OK) hs = walk_plan(P, mode, prec, A, stream);
+        if (hs == HG_OK) hs = grad_scratch_end(P, prec, grad, stream);
+    } else if (hs == HG_OK) {
+        hs = walk_plan(P, mode, prec, A, stream);
+    }
     free_plan(P, stream);
     return hs;
 }
@@ -1339,6 +1435,7 @@ extern "C" hg_status hg_rays_trace_gradient(hg_rays *r, double kappa, const doub
         set_error("hg_rays_trace_gradient: tau, ncross, w and grad_rho are required");
         return HG_EINVAL;
     }
+    if (r->n == 0) return HG_OK;
     TraceArgs A{};
     A.kappa = kappa;
     A.tau = tau;
@@ -1346,8 +1443,10 @@ extern "C" hg_status hg_rays_trace_gradient(hg_rays *r, double kappa, const doub
     A.status = ray_status;
     A.rho_ext = rho;
     A.w = w;
-    A.grad = grad_rho;
-    return walk_plan(*r, MODE_TAUADJ, precision | (grad_precision << 1), A, (cudaStream_t)stream);
+    hg_status st = grad_scratch_begin(*r, grad_precision, A, (cudaStream_t)stream);
+    if (st == HG_OK) st = walk_plan(*r, MODE_TAUADJ, precision | (grad_precision << 1), A, (cudaStream_t)stream);
+    if (st == HG_OK) st = grad_scratch_end(*r, grad_precision, grad_rho, (cudaStream_t)stream);
+    return st;
 }
 
 extern "C" hg_status hg_rays_trace_stage(hg_rays *r, double kappa, const double *rho, int32_t precision, void *tau,
@@ -1382,44 +1481,75 @@ extern "C" hg_status hg_rays_trace_stage(hg_rays *r, double kappa, const double 
     A.status = ray_status;
     A.rho_ext = rho;
     A.w = w;
-    A.grad = grad_rho;
-    st = w ? walk_plan(*r, MODE_TAUADJ_STAGE, precision | (grad_precision << 1), A, (cudaStream_t)stream)
-           : walk_plan(*r, MODE_TAU_STAGE, precision, A, (cudaStream_t)stream);
+    if (w) {
+        st = grad_scratch_begin(*r, grad_precision, A, (cudaStream_t)stream);
+        if (st == HG_OK)
+            st = walk_plan(*r, MODE_TAUADJ_STAGE, precision | (grad_precision << 1), A, (cudaStream_t)stream);
+        if (st == HG_OK) st = grad_scratch_end(*r, grad_precision, grad_rho, (cudaStream_t)stream);
+    } else {
+        st = walk_plan(*r, MODE_TAU_STAGE, precision, A, (cudaStream_t)stream);
+    }
     r->stg_prec = (st == HG_OK) ? precision : -1;
     return st;
 }
 
-extern "C" hg_status hg_rays_emit_staged(hg_rays *r, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
-                                         int64_t seg_capacity, uint8_t *ray_status, hg_stream stream) {
+// hg_rays_emit_staged (gp < 0) and hg_rays_emit_staged_gradient (gp 0: FP64
+// gradient, 1: FP32).
+static hg_status emit_staged(const char *name, hg_rays *r, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
+                             int64_t seg_capacity, uint8_t *ray_status, double kappa, const float *w, int gp,
+                             void *grad, cudaStream_t s) {
     if (!r) {
-        set_error("hg_rays_emit_staged: null rays");
+        set_error("%s: null rays", name);
         return HG_EINVAL;
     }
     if (r->stg_prec < 0) {
-        set_error("hg_rays_emit_staged: call hg_rays_trace_stage on these rays first");
+        set_error("%s: call hg_rays_trace_stage on these rays first", name);
         return HG_EINVAL;
     }
     if (r->n > 0 && (!seg_off || (seg_capacity > 0 && (!seg_cell || !seg_ds)) || seg_capacity < 0)) {
-        set_error("hg_rays_emit_staged: bad segment arrays");
+        set_error("%s: bad segment arrays", name);
+        return HG_EINVAL;
+    }
+    if (gp >= 0 && r->n > 0 && (!w || !grad)) {
+        set_error("%s: w and grad_rho are required", name);
         return HG_EINVAL;
     }
     if (r->n == 0) return HG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
+    TraceArgs B{};  // the adjoint: the copy's scatter, or the fallback gradient walk
+    B.kappa = kappa;
+    B.w = w;
+    B.run_if = r->stg_overflow;  // statuses stay those of the staged trace and the fill
+    if (gp >= 0) {
+        hg_status st = grad_scratch_begin(*r, gp, B, s);
+        if (st != HG_OK) return st;
+    }
     const int64_t gblocks = std::min<int64_t>((r->n * 8 + 255) / 256, (int64_t)sm_count() * 8);
-    if (r->stg_prec == HG_FP64)
-        gather_kernel<double><<<(unsigned)gblocks, 256, 0, s>>>(
-            r->n, r->starts, seg_off, r->stg_start_ray, r->list, r->splitting ? r->split_count : nullptr,
-            r->stg_start_seg, r->part_nc, r->stg_cell, static_cast<const double *>(r->stg_ds), r->stg_next,
-            r->stg_overflow, seg_cell, static_cast<double *>(seg_ds), seg_capacity, ray_status);
-    else
-        gather_kernel<float><<<(unsigned)gblocks, 256, 0, s>>>(
-            r->n, r->starts, seg_off, r->stg_start_ray, r->list, r->splitting ? r->split_count : nullptr,
-            r->stg_start_seg, r->part_nc, r->stg_cell, static_cast<const float *>(r->stg_ds), r->stg_next,
-            r->stg_overflow, seg_cell, static_cast<float *>(seg_ds), seg_capacity, ray_status);
+    const unsigned long long *sc = r->splitting ? r->split_count : nullptr;
+#define HG_GATHER(GP, DS)                                                                                          \
+    gather_kernel<GP, DS><<<(unsigned)gblocks, 256, 0, s>>>(                                                     \
+        r->n, r->starts, seg_off, r->stg_start_ray, r->list, sc, r->stg_start_seg, r->part_nc, r->stg_cell,     \
+        static_cast<const DS *>(r->stg_ds), r->stg_next, r->stg_overflow, seg_cell, static_cast<DS *>(seg_ds), \
+        seg_capacity, ray_status, kappa, w, B.grad, B.gmul, B.gmask)
+    if (r->stg_prec == HG_FP64) {
+        if (gp < 0)
+            HG_GATHER(-1, double);
+        else if (gp == 0)
+            HG_GATHER(0, double);
+        else
+            HG_GATHER(1, double);
+    } else {
+        if (gp < 0)
+            HG_GATHER(-1, float);
+        else if (gp == 0)
+            HG_GATHER(0, float);
+        else
+            HG_GATHER(1, float);
+    }
+#undef HG_GATHER
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(e, "gather launch");
-    // the fill walk runs only when the staging pool overflowed
+    // the fill walk (and the adjoint walk) run only when the staging pool overflowed
     TraceArgs A{};
     A.seg_off = seg_off;
     A.seg_cell = seg_cell;
@@ -1427,7 +1557,29 @@ extern "C" hg_status hg_rays_emit_staged(hg_rays *r, const int64_t *seg_off, int
     A.seg_cap = seg_capacity;
     A.status = ray_status;
     A.run_if = r->stg_overflow;
-    return walk_plan(*r, MODE_FILL, r->stg_prec, A, s);
+    hg_status st = walk_plan(*r, MODE_FILL, r->stg_prec, A, s);
+    if (st != HG_OK || gp < 0) return st;
+    st = walk_plan(*r, MODE_ADJ, gp, B, s);
+    if (st == HG_OK) st = grad_scratch_end(*r, gp, grad, s);
+    return st;
+}
+
+extern "C" hg_status hg_rays_emit_staged(hg_rays *r, const int64_t *seg_off, int32_t *seg_cell, void *seg_ds,
+                                         int64_t seg_capacity, uint8_t *ray_status, hg_stream stream) {
+    return emit_staged("hg_rays_emit_staged", r, seg_off, seg_cell, seg_ds, seg_capacity, ray_status, 0.0, nullptr,
+                       -1, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" hg_status hg_rays_emit_staged_gradient(hg_rays *r, const int64_t *seg_off, int32_t *seg_cell,
+                                                  void *seg_ds, int64_t seg_capacity, uint8_t *ray_status,
+                                                  double kappa, const float *w, int32_t grad_precision,
+                                                  void *grad_rho, hg_stream stream) {
+    if (grad_precision != 0 && grad_precision != 1) {
+        set_error("hg_rays_emit_staged_gradient: grad_precision must be 0 (f64) or 1 (f32)");
+        return HG_EINVAL;
+    }
+    return emit_staged("hg_rays_emit_staged_gradient", r, seg_off, seg_cell, seg_ds, seg_capacity, ray_status, kappa,
+                       w, grad_precision, grad_rho, (cudaStream_t)stream);
 }
 
 extern "C" hg_status hg_rays_fill(hg_rays *r, int32_t precision, const int64_t *seg_off, int32_t *seg_cell,
@@ -1471,11 +1623,14 @@ extern "C" hg_status hg_rays_gradient(hg_rays *r, double kappa, const float *w, 
         set_error("hg_rays_gradient: grad_precision must be 0 (f64) or 1 (f32)");
         return HG_EINVAL;
     }
+    if (r->n == 0) return HG_OK;
     TraceArgs A{};
     A.kappa = kappa;
     A.w = w;
-    A.grad = grad_rho;
-    return walk_plan(*r, MODE_ADJ, grad_precision, A, (cudaStream_t)stream);
+    hg_status st = grad_scratch_begin(*r, grad_precision, A, (cudaStream_t)stream);
+    if (st == HG_OK) st = walk_plan(*r, MODE_ADJ, grad_precision, A, (cudaStream_t)stream);
+    if (st == HG_OK) st = grad_scratch_end(*r, grad_precision, grad_rho, (cudaStream_t)stream);
+    return st;
 }
 
 extern "C" void hg_rays_free(hg_rays *r, hg_stream stream) {

@@ -648,6 +648,10 @@ struct WalkIO {
     int64_t seg_cap;
     const float *w;
     void *grad;
+    // gradient slot of leaf c: (c * gmul) mod 2^32 masked by gmask (identity by default); an odd
+    // multiplier scatters spatially close leaves over distinct L2 lines, so that the atomic adds of
+    // the many rays crossing a dense region do not queue on a few lines
+    uint32_t gmul = 1u, gmask = 0xffffffffu;
     const double *rho_ext;  // densities replacing the grid's own (MODE_TAU), or NULL
     // interaction points (MODE_INTERACT): drawn optical depths in, leaf and path parameter out
     const double *tau_int = nullptr;
@@ -853,10 +857,11 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                 }
                 if (ADJ) {
                     const double v = wk * ds;
+                    const uint32_t slot = ((uint32_t)S.cur * io.gmul) & io.gmask;
                     if (GPREC == 0)
-                        red_add_keep(static_cast<double *>(io.grad) + S.cur, v, keep);
+                        red_add_keep(static_cast<double *>(io.grad) + slot, v, keep);
                     else
-                        red_add_keep(static_cast<float *>(io.grad) + S.cur, __double2float_rn(v), keep);
+                        red_add_keep(static_cast<float *>(io.grad) + slot, __double2float_rn(v), keep);
                 }
                 nc++;
             }

@@ -325,7 +325,7 @@ def test_forced_segments_adjoint(hg, disk_grids, kind):
     g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 0.8)
     g, n = _launches(hg, lambda: hg.tau_gradient(grid, _cuda(o), _cuda(k), _cuda(w, torch.float32), kappa=0.8,
                                                  grad_precision="fp64", split="force"))
-    assert n == 5
+    assert n == 6  # setup, queue order, split planner, walk, combine, gradient slots to leaf order
     np.testing.assert_allclose(_np(g), g_ref, rtol=1e-12, atol=1e-300)
 
 
@@ -369,7 +369,7 @@ def test_prepared_rays_path_ends_and_gradient(hg, disk_grids, kind):
     w = synth.adjoint_weights(13, a.shape[0])
     g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 1.9)
     g, n = _launches(hg, lambda: R.gradient(_cuda(w, torch.float32), kappa=1.9, grad_precision="fp64"))
-    assert n == 2  # walk, combine
+    assert n == 3  # walk, combine, gradient slots to leaf order
     np.testing.assert_allclose(_np(g), g_ref, rtol=1e-12, atol=1e-300)
     # a second trace with other densities reuses the plan
     rho = torch.full((tree.n_leaves,), 2.0, dtype=torch.float64, device="cuda")
@@ -392,7 +392,7 @@ def test_fused_trace_and_gradient(hg, disk_grids, kind, split):
     R = hg.prepare_rays(grid, _cuda(o), _cuda(k), split=split, schedule=3)
     W = _cuda(w, torch.float32)
     (tau, nc, st, g64), n = _launches(hg, lambda: R.trace_gradient(W, kappa=1.2, grad_precision="fp64"))
-    assert n == (2 if split == "force" else 1)  # walk (, combine)
+    assert n == (3 if split == "force" else 2)  # walk (, combine), gradient slots to leaf order
     np.testing.assert_array_equal(_np(nc), ref["ncross"])
     np.testing.assert_array_equal(_np(st), ref["status"])
     _check_tau(_np(tau), ref["tau"], TAU_RTOL_FP64)
@@ -415,19 +415,67 @@ def test_fused_trace_and_gradient(hg, disk_grids, kind, split):
 @pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
 def test_single_pass_emission_bit_exact(hg, disk_grids, kind, split):
     # the trace stages every emitted cell; a copy puts them at the scanned offsets: the whole
-    # sequences and lengths must be the oracle's, with or without the gradient in the same walk
+    # sequences and lengths must be the oracle's, with or without the gradient, scattered in the
+    # walk or in the copy (from the staged lengths: FP32 ones after an FP32-Kahan trace)
     model, grids, o, k = disk_grids
     grid, tree, _ = grids[kind]
-    w = synth.adjoint_weights(23, o.shape[0])
+    w = synth.adjoint_weights(23, o.shape[0])  # in [0, 1): every adjoint term is >= 0
     ref = oracle.trace(tree, o, k, kappa=0.9, emit=True)
     g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 0.9)
     R = hg.prepare_rays(grid, _cuda(o), _cuda(k), split=split, schedule=3)
     W = _cuda(w, torch.float32)
-    for prec, with_w in (("fp64", True), ("fp32k", False), ("fp64", False), ("fp32k", True)):
-        out = R.emit_single_pass(kappa=0.9, precision=prec, w=W if with_w else None, grad_precision="fp64")
+    for prec, with_w, adj in (("fp64", True, "walk"), ("fp64", True, "copy"), ("fp32k", False, "copy"),
+                              ("fp64", False, "copy"), ("fp32k", True, "walk"), ("fp32k", True, "copy")):
+        out = R.emit_single_pass(kappa=0.9, precision=prec, w=W if with_w else None, grad_precision="fp64",
+                                 adjoint=adj)
         _same_emission(out, ref, prec)
         if with_w:
-            np.testing.assert_allclose(_np(out["grad"]), g_ref, rtol=1e-12, atol=1e-300)
+            # FP64 lengths: the oracle's terms, summed in another order; FP32 staged lengths: each
+            # term within 2^-24 relative, so the (non-negative) sum within 2^-23
+            rtol = 2.0 ** -23 if (prec == "fp32k" and adj == "copy") else 1e-12
+            np.testing.assert_allclose(_np(out["grad"]), g_ref, rtol=rtol, atol=1e-300)
+    R.free()
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_copy_adjoint_ignores_capacity_and_overflow(hg, disk_grids, kind):
+    # the adjoint scattered during the copy covers every crossing: when the emission capacity
+    # drops entries (their rays flagged HG_RAY_OVERFLOW), and when the staging pool overflowed
+    # (a fill walk and a gradient walk take over)
+    model, grids, o, k = disk_grids
+    grid, tree, _ = grids[kind]
+    a, kk, L = synth.endpoint_paths(82, 3001)
+    w = synth.adjoint_weights(24, a.shape[0])
+    ref = oracle.trace(tree, a, kk, smax=L, kappa=1.3, emit=True)
+    g_ref = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64), 1.3)
+    R = hg.prepare_rays(grid, _cuda(a), _cuda(kk), _cuda(L), split="force")
+    W = _cuda(w, torch.float32)
+    counts = np.bincount(ref["seg_cell"], minlength=tree.n_leaves).astype(np.float64)
+    u = 2.0 ** -24
+    gam32 = (counts + 1) * u / (1 - (counts + 1) * u)  # FP32 terms and FP32 running sums
+    for gp in ("fp64", "fp32"):
+        tau, nc, st, _ = R.trace_stage(kappa=1.3)
+        off = hg.scan_offsets(nc)
+        total = int(off[-1].item())
+        cap = total // 2
+        cell, ds, g = R.emit_staged_gradient(off, W, kappa=1.3, grad_precision=gp, capacity=cap, status=st)
+        if gp == "fp64":
+            np.testing.assert_allclose(_np(g), g_ref, rtol=1e-12, atol=1e-300)
+        else:
+            assert (np.abs(_np(g).astype(np.float64) - g_ref) <= gam32 * g_ref + 1e-30).all()
+        so = ref["seg_off"]
+        cut = (so[1:] > cap) & (so[1:] > so[:-1])  # rays with an entry at or beyond the capacity
+        np.testing.assert_array_equal((_np(st) & hg.RAY_OVERFLOW) != 0, cut)
+        np.testing.assert_array_equal(_np(cell)[:cap], ref["seg_cell"][:cap])
+        np.testing.assert_array_equal(_np(ds)[:cap], ref["seg_ds"][:cap])
+        assert cut.any() and not cut.all()
+    tau, nc, st, _ = R.trace_stage(kappa=1.3, stage_per_ray=-3)  # pool of 3 chunks: overflows
+    off = hg.scan_offsets(nc)
+    cell, ds, g = R.emit_staged_gradient(off, W, kappa=1.3, grad_precision="fp64", status=st)
+    np.testing.assert_array_equal(_np(cell), ref["seg_cell"])
+    np.testing.assert_array_equal(_np(ds), ref["seg_ds"])
+    np.testing.assert_array_equal(_np(st), ref["status"])
+    np.testing.assert_allclose(_np(g), g_ref, rtol=1e-12, atol=1e-300)
     R.free()
 
 
