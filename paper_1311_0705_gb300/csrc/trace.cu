@@ -166,8 +166,9 @@ struct SplitRec {
 // into K = min(16, ceil(w / W)) pieces of equal estimated work,
 // W = max(32, A / 2).  Forced: every ray of more than 3 estimated crossings,
 // W = 2.  One warp per ray, over the heavy end of the work-ordered queue:
-// every lane repeats the setup's march of the work lattice, lane j places
-// cut j (descent and depth test), and the accepted cuts are those of
+// the lanes sample the work lattice at 32 points of the path and sum them
+// (a warp prefix sum), lane j places cut j where the sum reaches (j + 1) / K
+// of the total (descent and depth test), and the accepted cuts are those of
 // increasing t_c in distinct leaves, in path order.  Segment slots are
 // taken with one atomic per ray; their count is bounded (sum over split
 // rays of ceil(w/W) <= total/W + total/max(64, A) <= 3 T, or 16 n when
@@ -219,16 +220,45 @@ __global__ void __launch_bounds__(256) split_kernel(const DevGrid G, int64_t n, 
         const float tend = R.t1;
         // cuts stay clear of both ends of the path
         const float lo_t = ts + (tend - ts) * 0x1p-10f, hi_t = tend - (tend - ts) * 0x1p-10f;
-        // cut time of this lane: where the estimated work reaches (lane + 1) / K of the total
-        const float target = R.work * (float)(lane + 1) / (float)K;
-        float tc = 0.0f;
-        bool found = false;
-        work_march(G, lat, of, kf, ts, tend, [&](float t, float tn, float rate, float e) {
-            if (!found && rate > 0.0f && e + rate * (tn - t) >= target) {
-                tc = t + (target - e) / rate;
-                found = true;
+        // cut time of this lane: where the estimated work reaches (lane + 1) / K of the total.  The
+        // estimate comes from 32 samples of the work lattice, lane i at the middle of the i-th of 32
+        // equal pieces of the walked interval; a warp prefix sum gives the work up to each piece's
+        // end, and a search over it the piece where the target falls (linear inside the piece).
+        // Coarser than a cell-by-cell march, which cost each warp ~1000 instructions per long path;
+        // the cuts only balance work.
+        const float dt = (tend - ts) * (1.0f / 32.0f);
+        float rate = 0.0f;
+        {
+            const int N = G.work_n;
+            const float tm = ts + ((float)lane + 0.5f) * dt;
+            int ci[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float lo = (float)G.dlo[a];
+                const float p = (of[a] + kf[a] * tm - lo) * ((float)N / ((float)G.dhi[a] - lo));
+                const int c = (int)floorf(p);
+                ci[a] = c < 0 ? 0 : (c > N - 1 ? N - 1 : c);
             }
-        });
+            rate = lat[ci[0] + N * (ci[1] + N * ci[2])];
+        }
+        float e = rate * dt;  // inclusive prefix sum over the pieces
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float v = __shfl_up_sync(0xffffffffu, e, off);
+            if (lane >= off) e += v;
+        }
+        const float E = __shfl_sync(0xffffffffu, e, 31);
+        const float target = E * (float)(lane + 1) / (float)K;
+        int pos = 0;  // first piece whose prefix reaches the target
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const float v = __shfl_sync(0xffffffffu, e, pos + step - 1);
+            if (v < target) pos += step;
+        }
+        const float e_before = __shfl_sync(0xffffffffu, e, pos > 0 ? pos - 1 : 0);
+        const float r_pos = __shfl_sync(0xffffffffu, rate, pos);
+        const bool found = E > 0.0f && r_pos > 0.0f;
+        const float tc = found ? ts + (float)pos * dt + (target - (pos > 0 ? e_before : 0.0f)) / r_pos : 0.0f;
         // the leaf containing o + d t_c, and whether the point lies deep inside it
         bool ok = false;
         int32_t Lid = -1;
@@ -684,7 +714,8 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
     P.smem = (size_t)smem_nodes * node_bytes;
     int64_t blocks = 0;
-    hg_status hs = walk_blocks(pick_kernel(g->d.kind, MODE_TAU, HG_FP64, min_blocks), block, P.smem, n, blocks);
+    const KernelFn k0 = pick_kernel(g->d.kind, MODE_TAU, HG_FP64, min_blocks);
+    hg_status hs = walk_blocks(k0, block, P.smem, n, blocks);
     if (hs != HG_OK) return hs;
     P.threads = blocks * block;
     // auto schedule: order by estimated work only when each resident thread
@@ -693,6 +724,11 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     P.dyn = (schedule >= 2);
     P.ordered = (schedule == 3);
     P.splitting = P.ordered && allow_split && split != HG_SPLIT_OFF && g->d.work;
+    if (P.splitting) {  // segments add queue items: the walks run every resident thread
+        hs = walk_blocks(k0, block, P.smem, INT64_MAX / 2, blocks);
+        if (hs != HG_OK) return hs;
+        P.threads = blocks * block;
+    }
     P.seg_cap = P.splitting ? std::min<int64_t>((split == HG_SPLIT_FORCE ? 16 * n : 3 * P.threads) + 1024, 16 * n)
                             : 0;
     // scratch: start records; the queue counter; for the ordered schedule the
@@ -987,7 +1023,7 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
     const hg_grid *g = P.g;
     KernelFn k = pick_kernel(g->d.kind, mode, prec, P.min_blocks);
     int64_t blocks = 0;
-    hg_status hs = walk_blocks(k, P.block, P.smem, P.n, blocks);
+    hg_status hs = walk_blocks(k, P.block, P.smem, P.splitting ? INT64_MAX / 2 : P.n, blocks);
     if (hs != HG_OK) return hs;
     A.G = g->d;
     A.n = P.n;
