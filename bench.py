@@ -303,42 +303,64 @@ def run_ours(args):
 
     kev = []  # (start, end) events around the dominant kernel
     cev = []  # (start, end) events around the emission copy with the adjoint scatter
+    gstreams = [torch.cuda.Stream(device=dev) for _ in grids]
+
+    def on_grid_streams(fn):
+        # fn(g) for every grid, each on its own stream after the work queued so far; then join
+        for gs, g in zip(gstreams, grids):
+            gs.wait_stream(stream)
+            with torch.cuda.stream(gs):
+                fn(g)
+        for gs in gstreams:
+            stream.wait_stream(gs)
 
     def step(record=False):
+        # per grid: one setup (first leaf, work-ordered queue, path segments) for the emission rays;
+        # one walk for the optical depth, counts and the staged emission; then the emission copy,
+        # which also scatters the adjoint from the staged lengths, and the quality metrics.  The two
+        # grids' setups run concurrently on their own streams, the two walks run alone one after
+        # the other (so that their event times are theirs), and the rest of each grid runs
+        # concurrently again.
         out = {}
-        for g in grids:
-            G = g["grid"]
-            # one setup (first leaf, work-ordered queue, path segments) for these rays; one walk for
-            # the optical depth, counts and the staged emission; then the emission copy, which also
-            # scatters the adjoint from the staged lengths
-            R = hg.prepare_rays(G, O, K)
+
+        def prep(g):
+            g["R"] = hg.prepare_rays(g["grid"], O, K)
             g["grad"].zero_()
-            if record:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            R.trace_stage(kappa=1.0, precision=prec, out=(g["tau"], g["nc"], g["st"]))
-            if record:
-                e1.record(stream)
-                kev.append((g["name"], e0, e1))
+
+        def rest(g):
+            G, R = g["grid"], g["R"]
             ncs = hg.sum_i32(g["nc"])
             off = hg.scan_offsets(g["nc"])
             cap = g.get("cap")
             if cap is None:
                 cap = g["cap"] = int(off[-1].item())
+            gs = torch.cuda.current_stream()
             if record:
                 c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                c0.record(stream)
+                c0.record(gs)
             cell, ds, _ = R.emit_staged_gradient(off, W, kappa=1.0, grad=g["grad"], grad_precision="fp32",
                                                  capacity=cap, status=g["st"])
             if record:
-                c1.record(stream)
+                c1.record(gs)
                 cev.append((g["name"], c0, c1))
             _, rg = hg.sample_density(G, P)
             drho = hg.diff_stats(RT, rg)
             ptau, _, _ = hg.trace_rays(G, PA, PK, PL, kappa=1.0, precision="fp64", out=(g["ptau"], g["pnc"], None))
             dtau = hg.diff_stats(TT, ptau)
             R.free()
+            g["R"] = None
             out[g["name"]] = (ncs, drho, dtau)
+
+        on_grid_streams(prep)
+        for g in grids:
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            g["R"].trace_stage(kappa=1.0, precision=prec, out=(g["tau"], g["nc"], g["st"]))
+            if record:
+                e1.record(stream)
+                kev.append((g["name"], e0, e1))
+        on_grid_streams(rest)
         return out
 
     for _ in range(args.warmup):
