@@ -218,6 +218,8 @@ WORKLOADS = {
     "interact-1e6": ("disk, octree and k-d tree as disk-1e6; 1e6 photon packets per grid walked to their interaction "
                      "point (tau_int = -ln u), kappa 200 (face-on tau 12, edge-on ~100 at the centre)",
                      make_disk_grids),
+    "build-1e6": ("disk-1e6's octree and k-d tree (mass 1e-6, max level 12) built on the GPU: Monte Carlo node "
+                  "evaluation (100 draws per node) and neighbor lists on the device, children on the host", None),
 }
 # opacity of the interaction workload: the disk optically thick in its midplane
 INTERACT_KAPPA = 200.0
@@ -865,6 +867,98 @@ def run_interact(args):
         dist.destroy_process_group()
 
 
+def run_build(args):
+    """Tree construction on the GPU (hg_build_grid_gpu) of the disk-1e6 octree and k-d tree; value = nodes
+    built per second.  The call takes a host model description and returns host arrays, so the timed
+    step is end to end; the host builder (all cores) and the oracle's builder are timed beside it."""
+    import torch
+    import paper_1311_0705_gb300 as hg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    desc, _ = WORKLOADS[args.workload]
+    specs = []
+    for kind in (synth.TREE_OCTREE, synth.TREE_KD):
+        model, bp, _, _ = synth.workload_disk_1e6(kind)
+        specs.append(("octree" if kind == 0 else "kd", model, bp))
+    stream = torch.cuda.current_stream()
+    sizes = {}
+
+    def step(record=None):
+        for name, model, bp in specs:
+            if record is not None:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            G = hg.build_grid_gpu(model, bp)
+            if record is not None:
+                e1.record(stream)
+                record.append((name, e0, e1))
+            sizes[name] = (G.n_nodes, G.n_leaves, int(G.nbr_off[-1]))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = hg.launch_count()
+    barrier(dist, dev)
+    torch.cuda.synchronize()
+    ev = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(ev)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(dist, dev)
+    launches = hg.launch_count() - l0
+    clk = clocks.stop()
+    per = {}
+    for name, a, b in ev:
+        per.setdefault(name, []).append(a.elapsed_time(b))
+    tot_ms = max_over_ranks(dist, sum(sum(v) for v in per.values()), dev)
+    nodes = sum(v[0] for v in sizes.values())
+    value = sum_over_ranks(dist, nodes * args.steps, dev) / (tot_ms / 1e3)
+    grids = {}
+    for name, model, bp in specs:
+        t = time.perf_counter()
+        hg.build_grid(model, bp)
+        host_s = time.perf_counter() - t
+        n, nl, ne = sizes[name]
+        ms = statistics.mean(per[name])
+        grids[name] = dict(nodes=n, leaves=nl, list_entries=ne, gpu_build_ms=ms, host_build_ms=host_s * 1e3,
+                           nodes_per_s=n / ms * 1e3)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        name, model, bp = specs[1]  # the k-d tree: 2.9e6 nodes, a few seconds single-threaded
+        t = time.perf_counter()
+        T = oracle.build_tree(model, bp)
+        dt = time.perf_counter() - t
+        cpu = dict(value=T.n_nodes / dt, unit="nodes/s", cores=1, kind="oracle",
+                   sample=f"the oracle's builder on the k-d grid ({T.n_nodes} nodes, node list and statistics; "
+                          "the oracle has no neighbor lists)")
+    per_node_h2d = 3 * 4 + 3 * 8  # levels and indices of each node, uploaded level by level
+    h2d = sum(v[0] * (per_node_h2d + 4 + 4 + 3 * 8) + v[1] * 8 for v in sizes.values())
+    d2h = sum(v[0] * 48 + (6 * v[1] + 1) * 8 + v[2] * 4 for v in sizes.values())
+    line = dict(metric=METRIC, value=value, unit="nodes/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=tot_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, description=desc, grids=grids,
+                            wall_ms_per_step=wall / args.steps * 1e3,
+                            timing="CUDA events on the builder's stream around each (synchronous) build call"),
+                roofline=None, cpu_baseline=cpu,
+                e2e=dict(value=value, unit="nodes/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                         note="the build call is host to host: the timed step already includes its copies"),
+                gpu_launches=int(launches),
+                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(model, grids, o, k, pts, pa, pk, pl, w, sample: int = 200_000):
     import oracle
     threads = os.cpu_count() or 1
@@ -945,6 +1039,8 @@ def main(argv=None):
         run_batch(args)
     elif args.workload == "interact-1e6":
         run_interact(args)
+    elif args.workload == "build-1e6":
+        run_build(args)
     else:
         run_ours(args)
 

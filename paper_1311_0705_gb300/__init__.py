@@ -94,6 +94,7 @@ _I64 = C.c_int64
 _S = C.c_int  # hg_status
 _SIGS = {
     "hg_build_grid": (_S, [C.POINTER(_Model), C.POINTER(_BuildParams), C.c_int32, C.POINTER(_V)]),
+    "hg_build_grid_gpu": (_S, [C.POINTER(_Model), C.POINTER(_BuildParams), _V, C.POINTER(_V)]),
     "hg_tau_max_recipe": (_S, [C.POINTER(_Model), C.POINTER(_BuildParams), C.c_double, C.c_int32,
                                C.POINTER(C.c_double)]),
     "hg_host_grid_desc": (_S, [_V, C.POINTER(_Desc)]),
@@ -291,6 +292,16 @@ def build_grid(model, params, threads: int = 0) -> HostGrid:
     p = _build_params(params)
     h = C.c_void_p()
     _check(_lib.hg_build_grid(C.byref(m), C.byref(p), int(threads), C.byref(h)), "hg_build_grid")
+    return HostGrid(h)
+
+
+def build_grid_gpu(model, params) -> HostGrid:
+    """hg_build_grid_gpu: the node list with its Monte Carlo node evaluation on the current GPU
+    (one thread per node, a level per launch) and the neighbor lists (one thread per leaf wall)."""
+    m, _keep = _model_struct(model)
+    p = _build_params(params)
+    h = C.c_void_p()
+    _check(_lib.hg_build_grid_gpu(C.byref(m), C.byref(p), _stream(), C.byref(h)), "hg_build_grid_gpu")
     return HostGrid(h)
 
 

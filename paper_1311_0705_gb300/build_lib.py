@@ -27,6 +27,7 @@ UNITS = [
     ("trace.cu", True),
     ("batch.cu", True),
     ("noalloc.cu", True),
+    ("gbuild.cu", True),
     ("metrics.cu", False),
     ("grid.cpp", False),
     ("build.cpp", False),

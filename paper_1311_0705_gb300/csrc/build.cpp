@@ -18,29 +18,10 @@
 #include <thread>
 
 #include "hg_internal.h"
+#include "gbuild.h"
+#include "model_eval.h"
 
 namespace {
-
-constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
-
-// SplitMix64 output function (Steele, Lea & Flood 2014).
-inline uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-    return z ^ (z >> 31);
-}
-
-inline uint64_t box_key(uint64_t seed, const int32_t *l, const int64_t *i) {
-    uint64_t lv = (uint64_t)l[0] | ((uint64_t)l[1] << 8) | ((uint64_t)l[2] << 16);
-    uint64_t k = mix64(seed + kGamma * (1ULL + lv));
-    k = mix64(k + kGamma * (1ULL + (uint64_t)i[0]));
-    k = mix64(k + kGamma * (1ULL + (uint64_t)i[1]));
-    return mix64(k + kGamma * (1ULL + (uint64_t)i[2]));
-}
-
-inline double unit_draw(uint64_t key, uint64_t j) {
-    return (double)(mix64(key + kGamma * (j + 1ULL)) >> 11) * 0x1.0p-53;
-}
 
 template <class F>
 void parallel_for(int64_t n, int threads, F &&fn) {
@@ -116,94 +97,25 @@ struct HostModel {
         for (int64_t c = 0; c < nc; c++) std::copy(lists[c].begin(), lists[c].end(), cell_ids.begin() + cell_off[c]);
     }
 
-    double rho(double x, double y, double z) const {
-        switch (m.kind) {
-        case HG_MODEL_CONST:
-            return m.p[0];
-        case HG_MODEL_DISK: {
-            double R = std::sqrt(x * x + y * y);
-            double e = -(R / m.p[1]) - (std::fabs(z) / m.p[2]);
-            return m.p[0] * std::exp(e);
+    // the model as the node evaluation reads it (pointers into this object)
+    hg::ModelView view() const {
+        hg::ModelView v;
+        v.kind = m.kind;
+        v.n_table = m.n_table;
+        for (int j = 0; j < 8; j++) v.p[j] = m.p[j];
+        for (int a = 0; a < 3; a++) {
+            v.lo[a] = m.lo[a];
+            v.hi[a] = m.hi[a];
         }
-        case HG_MODEL_TORUS: {
-            double s = std::sqrt(x * x + y * y) - m.p[0];
-            double v = (s * s + z * z < m.p[1] * m.p[1]) ? m.p[2] : 0.0;
-            if (m.n_table <= 0) return v;
-            double pos[3] = {x, y, z};
-            int ix[3];
-            for (int a = 0; a < 3; a++) {
-                int q = (int)std::floor((pos[a] - m.lo[a]) / (m.hi[a] - m.lo[a]) * G);
-                ix[a] = q < 0 ? 0 : (q >= G ? G - 1 : q);
-            }
-            size_t c = (size_t)ix[0] + G * ((size_t)ix[1] + G * ix[2]);
-            for (int32_t e = cell_off[c]; e < cell_off[c + 1]; e++) {
-                const double *cl = &table[5 * (size_t)cell_ids[e]];
-                double dx = x - cl[0], dy = y - cl[1], dz = z - cl[2];
-                double r2 = dx * dx + dy * dy + dz * dz;
-                double s2 = cl[3] * cl[3];
-                if (r2 < 25.0 * s2) v += cl[4] * std::exp(-0.5 * (r2 / s2));
-            }
-            return v;
-        }
-        case HG_MODEL_DYADIC: {
-            int L = (int)m.p[0];
-            int64_t n = (int64_t)1 << L;
-            double pos[3] = {x, y, z};
-            int64_t ix[3];
-            for (int a = 0; a < 3; a++) {
-                double f = (pos[a] - m.lo[a]) / (m.hi[a] - m.lo[a]) * (double)n;
-                int64_t q = (int64_t)std::floor(f);
-                ix[a] = q < 0 ? 0 : (q > n - 1 ? n - 1 : q);
-            }
-            return m.table[ix[0] + n * (ix[1] + n * ix[2])];
-        }
-        }
-        return 0.0;
+        v.m_tot = m.m_tot;
+        v.table = table.data();
+        v.G = G;
+        v.cell_off = cell_off.empty() ? nullptr : cell_off.data();
+        v.cell_ids = cell_ids.empty() ? nullptr : cell_ids.data();
+        return v;
     }
 
-    // lo + (hi - lo) * i / 2^l on axis a, the top end being hi itself
-    double bound(int a, int64_t i, int32_t l) const {
-        if (i == ((int64_t)1 << l)) return m.hi[a];
-        return m.lo[a] + (m.hi[a] - m.lo[a]) * std::ldexp((double)i, -l);
-    }
 };
-
-struct Stats {
-    double rho, mass, delta, tau, q;
-    bool sub;
-};
-
-Stats eval_node(const HostModel &M, const hg_build_params &P, const int32_t *l, const int64_t *i, int32_t depth) {
-    double lo[3], hi[3];
-    for (int a = 0; a < 3; a++) {
-        lo[a] = M.bound(a, i[a], l[a]);
-        hi[a] = M.bound(a, i[a] + 1, l[a]);
-    }
-    const uint64_t key = box_key(P.seed, l, i);
-    double S = 0.0, rmin = 0.0, rmax = 0.0;
-    for (int32_t s = 0; s < P.n_ran; s++) {
-        double x = lo[0] + unit_draw(key, 3ULL * s) * (hi[0] - lo[0]);
-        double y = lo[1] + unit_draw(key, 3ULL * s + 1) * (hi[1] - lo[1]);
-        double z = lo[2] + unit_draw(key, 3ULL * s + 2) * (hi[2] - lo[2]);
-        double r = M.rho(x, y, z);
-        S += r;
-        if (s == 0 || r < rmin) rmin = r;
-        if (s == 0 || r > rmax) rmax = r;
-    }
-    Stats st;
-    double a = hi[0] - lo[0], b = hi[1] - lo[1], c = hi[2] - lo[2];
-    double V = a * b * c;
-    st.rho = S / (double)P.n_ran;
-    st.mass = V * st.rho;
-    st.delta = st.mass / M.m.m_tot;
-    st.tau = P.kappa * st.mass * std::sqrt(a * a + b * b + c * c) / (a * b * c);
-    st.q = (rmax > 0.0) ? (rmax - rmin) / rmax : 0.0;
-    bool at_max = (P.kind == HG_OCTREE) ? (l[0] >= P.max_level) : (depth >= 3 * P.max_level);
-    bool sub = (P.use_delta && st.delta > P.delta_max) || (P.use_tau && st.tau > P.tau_max) ||
-               (P.use_q && st.q > P.q_max);
-    st.sub = sub && !at_max;
-    return st;
-}
 
 }  // namespace
 
@@ -298,115 +210,176 @@ void build_neighbors(hg_host_grid &G, int threads) {
 
 }  // namespace
 
-extern "C" hg_status hg_build_grid(const hg_model *model, const hg_build_params *params, int32_t n_threads,
-                                   hg_host_grid **out) {
+namespace {
+
+hg_status check_build_args(const char *name, const hg_model *model, const hg_build_params *params, void *out) {
     if (!model || !params || !out) {
-        hg::set_error("hg_build_grid: null argument");
+        hg::set_error("%s: null argument", name);
         return HG_EINVAL;
     }
-    *out = nullptr;
-    const hg_build_params P = *params;
+    const hg_build_params &P = *params;
     if (P.kind != HG_OCTREE && P.kind != HG_KDTREE) { hg::set_error("bad tree kind %d", P.kind); return HG_EINVAL; }
     if (P.n_ran < 1 || P.max_level < 0 || P.max_level > 20) {
-        hg::set_error("hg_build_grid: n_ran must be >= 1 and max_level in 0..20");
+        hg::set_error("%s: n_ran must be >= 1 and max_level in 0..20", name);
         return HG_EINVAL;
     }
-    if (!(model->m_tot > 0.0)) { hg::set_error("hg_build_grid: m_tot must be > 0"); return HG_EINVAL; }
+    if (!(model->m_tot > 0.0)) { hg::set_error("%s: m_tot must be > 0", name); return HG_EINVAL; }
     if (model->kind < HG_MODEL_CONST || model->kind > HG_MODEL_DYADIC) {
-        hg::set_error("hg_build_grid: bad model kind %d", model->kind);
+        hg::set_error("%s: bad model kind %d", name, model->kind);
         return HG_EINVAL;
     }
     if ((model->kind == HG_MODEL_TORUS || model->kind == HG_MODEL_DYADIC) && model->n_table > 0 && !model->table) {
-        hg::set_error("hg_build_grid: model table missing");
+        hg::set_error("%s: model table missing", name);
         return HG_EINVAL;
     }
     for (int a = 0; a < 3; a++)
-        if (!(model->hi[a] > model->lo[a])) { hg::set_error("hg_build_grid: empty domain"); return HG_EINVAL; }
-    int threads = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+        if (!(model->hi[a] > model->lo[a])) { hg::set_error("%s: empty domain", name); return HG_EINVAL; }
+    return HG_OK;
+}
 
+// The node list, level by level: eval(begin, end, st) evaluates nodes
+// [begin, end) (their levels and indices are in G), then the nodes to
+// subdivide get their children appended in parent order.  Leaves are
+// numbered in node order (the caller builds the neighbor lists).
+template <class Eval>
+hg_status build_levels(const HostModel &M, const hg_build_params &P, hg_host_grid &G, Eval &&eval) {
+    const hg::ModelView V = M.view();
+    auto push = [&](const int32_t *l, const int64_t *i) {
+        for (int a = 0; a < 3; a++) {
+            G.lvl.push_back(l[a]);
+            G.idx.push_back(i[a]);
+            G.lo.push_back(hg::model_bound(V, a, i[a], l[a]));
+            G.hi.push_back(hg::model_bound(V, a, i[a] + 1, l[a]));
+        }
+        G.child.push_back(-1);
+        G.leaf.push_back(-1);
+    };
+    G.kind = P.kind;
+    int32_t l0[3] = {0, 0, 0};
+    int64_t i0[3] = {0, 0, 0};
+    push(l0, i0);
+    int64_t begin = 0;
+    std::vector<hg::NodeStats> st;
+    while (begin < (int64_t)G.child.size()) {
+        const int64_t end = (int64_t)G.child.size();
+        st.assign((size_t)(end - begin), hg::NodeStats{});
+        hg_status hs = eval(begin, end, st);
+        if (hs != HG_OK) return hs;
+        for (int64_t j = 0; j < end - begin; j++) {
+            G.rho.push_back(st[j].rho);
+            G.mass.push_back(st[j].mass);
+            G.delta.push_back(st[j].delta);
+            G.tau.push_back(st[j].tau);
+            G.q.push_back(st[j].q);
+        }
+        for (int64_t nd = begin; nd < end; nd++) {
+            if (!st[nd - begin].sub) continue;
+            const int nch = (P.kind == HG_OCTREE) ? 8 : 2;
+            if (P.max_nodes > 0 && (int64_t)G.child.size() + nch > P.max_nodes) {
+                hg::set_error("hg_build_grid: more than max_nodes=%lld nodes", (long long)P.max_nodes);
+                return HG_EOVERFLOW;
+            }
+            if ((int64_t)G.child.size() + nch > INT32_MAX) {
+                hg::set_error("hg_build_grid: node count exceeds int32 ids");
+                return HG_EOVERFLOW;
+            }
+            G.child[nd] = (int32_t)G.child.size();
+            int32_t l[3] = {G.lvl[3 * nd], G.lvl[3 * nd + 1], G.lvl[3 * nd + 2]};
+            int64_t i[3] = {G.idx[3 * nd], G.idx[3 * nd + 1], G.idx[3 * nd + 2]};
+            const int axis = (P.kind == HG_OCTREE) ? -1 : (l[0] + l[1] + l[2]) % 3;
+            for (int c = 0; c < nch; c++) {
+                int32_t lc[3] = {l[0], l[1], l[2]};
+                int64_t ic[3] = {i[0], i[1], i[2]};
+                if (axis < 0) {
+                    for (int a = 0; a < 3; a++) {
+                        lc[a] = l[a] + 1;
+                        ic[a] = 2 * i[a] + ((c >> a) & 1);
+                    }
+                } else {
+                    lc[axis] = l[axis] + 1;
+                    ic[axis] = 2 * i[axis] + c;
+                }
+                push(lc, ic);
+            }
+        }
+        begin = end;
+    }
+    const int64_t n = (int64_t)G.child.size();
+    for (int64_t nd = 0; nd < n; nd++)
+        if (G.child[nd] < 0) {
+            G.leaf[nd] = (int32_t)G.leaf_node.size();
+            G.leaf_node.push_back(nd);
+            G.leaf_rho.push_back(G.rho[nd]);
+        }
+    return HG_OK;
+}
+
+int host_threads(int32_t n_threads) {
+    return n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+}
+
+}  // namespace
+
+extern "C" hg_status hg_build_grid(const hg_model *model, const hg_build_params *params, int32_t n_threads,
+                                   hg_host_grid **out) {
+    hg_status hs = check_build_args("hg_build_grid", model, params, out);
+    if (hs != HG_OK) return hs;
+    *out = nullptr;
+    const hg_build_params P = *params;
+    const int threads = host_threads(n_threads);
     std::unique_ptr<hg_host_grid> G(new hg_host_grid());
     HostModel M;
     try {
         M.init(*model);
-        G->kind = P.kind;
-        auto push = [&](const int32_t *l, const int64_t *i) {
-            for (int a = 0; a < 3; a++) {
-                G->lvl.push_back(l[a]);
-                G->idx.push_back(i[a]);
-                G->lo.push_back(M.bound(a, i[a], l[a]));
-                G->hi.push_back(M.bound(a, i[a] + 1, l[a]));
-            }
-            G->child.push_back(-1);
-            G->leaf.push_back(-1);
-        };
-        int32_t l0[3] = {0, 0, 0};
-        int64_t i0[3] = {0, 0, 0};
-        push(l0, i0);
-        int64_t begin = 0;
-        std::vector<Stats> st;
-        while (begin < (int64_t)G->child.size()) {
-            const int64_t end = (int64_t)G->child.size();
-            st.assign((size_t)(end - begin), Stats{});
+        const hg::ModelView V = M.view();
+        hs = build_levels(M, P, *G, [&](int64_t begin, int64_t end, std::vector<hg::NodeStats> &st) {
             parallel_for(end - begin, threads, [&](int64_t a0, int64_t a1) {
                 for (int64_t j = a0; j < a1; j++) {
                     const int64_t nd = begin + j;
                     const int32_t *l = &G->lvl[3 * nd];
                     const int64_t *i = &G->idx[3 * nd];
-                    int32_t depth = (P.kind == HG_OCTREE) ? l[0] : l[0] + l[1] + l[2];
-                    st[j] = eval_node(M, P, l, i, depth);
+                    const int32_t depth = (P.kind == HG_OCTREE) ? l[0] : l[0] + l[1] + l[2];
+                    st[j] = hg::eval_node_stats(V, P, l, i, depth);
                 }
             });
-            for (int64_t j = 0; j < end - begin; j++) {
-                G->rho.push_back(st[j].rho);
-                G->mass.push_back(st[j].mass);
-                G->delta.push_back(st[j].delta);
-                G->tau.push_back(st[j].tau);
-                G->q.push_back(st[j].q);
-            }
-            for (int64_t nd = begin; nd < end; nd++) {
-                if (!st[nd - begin].sub) continue;
-                const int nch = (P.kind == HG_OCTREE) ? 8 : 2;
-                if (P.max_nodes > 0 && (int64_t)G->child.size() + nch > P.max_nodes) {
-                    hg::set_error("hg_build_grid: more than max_nodes=%lld nodes", (long long)P.max_nodes);
-                    return HG_EOVERFLOW;
-                }
-                if ((int64_t)G->child.size() + nch > INT32_MAX) {
-                    hg::set_error("hg_build_grid: node count exceeds int32 ids");
-                    return HG_EOVERFLOW;
-                }
-                G->child[nd] = (int32_t)G->child.size();
-                int32_t l[3] = {G->lvl[3 * nd], G->lvl[3 * nd + 1], G->lvl[3 * nd + 2]};
-                int64_t i[3] = {G->idx[3 * nd], G->idx[3 * nd + 1], G->idx[3 * nd + 2]};
-                const int axis = (P.kind == HG_OCTREE) ? -1 : (l[0] + l[1] + l[2]) % 3;
-                for (int c = 0; c < nch; c++) {
-                    int32_t lc[3] = {l[0], l[1], l[2]};
-                    int64_t ic[3] = {i[0], i[1], i[2]};
-                    if (axis < 0) {
-                        for (int a = 0; a < 3; a++) {
-                            lc[a] = l[a] + 1;
-                            ic[a] = 2 * i[a] + ((c >> a) & 1);
-                        }
-                    } else {
-                        lc[axis] = l[axis] + 1;
-                        ic[axis] = 2 * i[axis] + c;
-                    }
-                    push(lc, ic);
-                }
-            }
-            begin = end;
-        }
-        const int64_t n = (int64_t)G->child.size();
-        for (int64_t nd = 0; nd < n; nd++)
-            if (G->child[nd] < 0) {
-                G->leaf[nd] = (int32_t)G->leaf_node.size();
-                G->leaf_node.push_back(nd);
-                G->leaf_rho.push_back(G->rho[nd]);
-            }
-        build_neighbors(*G, threads);
+            return HG_OK;
+        });
+        if (hs == HG_OK) build_neighbors(*G, threads);
     } catch (const std::bad_alloc &) {
         hg::set_error("hg_build_grid: out of host memory");
         return HG_ENOMEM;
     }
+    if (hs != HG_OK) return hs;
+    *out = G.release();
+    return HG_OK;
+}
+
+extern "C" hg_status hg_build_grid_gpu(const hg_model *model, const hg_build_params *params, hg_stream stream,
+                                       hg_host_grid **out) {
+    hg_status hs = check_build_args("hg_build_grid_gpu", model, params, out);
+    if (hs != HG_OK) return hs;
+    *out = nullptr;
+    const hg_build_params P = *params;
+    std::unique_ptr<hg_host_grid> G(new hg_host_grid());
+    HostModel M;
+    hg::GpuNodeEval *E = nullptr;
+    try {
+        M.init(*model);
+        hs = hg::gpu_eval_create(M.view(), stream, &E);
+        if (hs == HG_OK)
+            hs = build_levels(M, P, *G, [&](int64_t begin, int64_t end, std::vector<hg::NodeStats> &st) {
+                return hg::gpu_eval_level(E, P, end - begin, &G->lvl[3 * begin], &G->idx[3 * begin], st.data());
+            });
+        if (hs == HG_OK)
+            hs = hg::gpu_build_neighbors(G->kind, (int64_t)G->child.size(), (int64_t)G->leaf_node.size(),
+                                         G->lvl.data(), G->idx.data(), G->child.data(), G->leaf.data(),
+                                         G->leaf_node.data(), stream, G->nbr_off, G->nbr_id);
+    } catch (const std::bad_alloc &) {
+        hg::set_error("hg_build_grid_gpu: out of host memory");
+        hs = HG_ENOMEM;
+    }
+    hg::gpu_eval_free(E);
+    if (hs != HG_OK) return hs;
     *out = G.release();
     return HG_OK;
 }
