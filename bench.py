@@ -219,7 +219,7 @@ WORKLOADS = {
                      "point (tau_int = -ln u), kappa 200 (face-on tau 12, edge-on ~100 at the centre)",
                      make_disk_grids),
     "build-1e6": ("disk-1e6's octree and k-d tree (mass 1e-6, max level 12) built on the GPU: Monte Carlo node "
-                  "evaluation (100 draws per node) and neighbor lists on the device, children on the host", None),
+                  "evaluation (100 draws per node), children and neighbor lists on the device", None),
 }
 # opacity of the interaction workload: the disk optically thick in its midplane
 INTERACT_KAPPA = 200.0

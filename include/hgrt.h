@@ -141,16 +141,16 @@ hg_status hg_build_grid(const hg_model *model, const hg_build_params *params, in
 /* hg_build_grid on the current GPU: every level of the breadth-first node
  * list (Sect. 2.2) has its nodes' n_ran Monte Carlo draws, mass, optical
  * depth and dispersion (Eq. 1-3) computed by one device thread per node,
- * with the host builder's draws and arithmetic; the host appends the
- * children; the neighbor lists (Sect. 2.3) are found by one device thread
- * per leaf wall.  All on `stream`.  Same tree, statistics and lists as
+ * with the host builder's draws and arithmetic, and its children appended
+ * by a scan; the neighbor lists (Sect. 2.3) are found by one device thread
+ * per leaf wall.  All on `stream`, one copy to the host at the end.  Same
+ * tree, statistics and lists as
  * hg_build_grid except that CUDA's exp may round differently from the
  * host's libm in the disk and clump models (a statistic then differs in its
  * last bits, and a node whose criterion lies that close to its threshold
  * may be decided the other way).  Synchronous: returns when the grid is
- * built.  Device memory used: the model table and clump index, 60 bytes per
- * node of the largest level, then 48 bytes per node and 36 per leaf plus
- * 12 per list entry for the lists. */
+ * built.  Device memory used: the model table and clump index, about 150
+ * bytes per node and 36 per leaf, then 12 per neighbor-list entry. */
 hg_status hg_build_grid_gpu(const hg_model *model, const hg_build_params *params, hg_stream stream,
                             hg_host_grid **out);
 /* The tau_max recipe of Sect. 4.1: build with params' mass criterion only

@@ -361,25 +361,32 @@ extern "C" hg_status hg_build_grid_gpu(const hg_model *model, const hg_build_par
     *out = nullptr;
     const hg_build_params P = *params;
     std::unique_ptr<hg_host_grid> G(new hg_host_grid());
-    HostModel M;
-    hg::GpuNodeEval *E = nullptr;
     try {
+        HostModel M;
         M.init(*model);
-        hs = hg::gpu_eval_create(M.view(), stream, &E);
-        if (hs == HG_OK)
-            hs = build_levels(M, P, *G, [&](int64_t begin, int64_t end, std::vector<hg::NodeStats> &st) {
-                return hg::gpu_eval_level(E, P, end - begin, &G->lvl[3 * begin], &G->idx[3 * begin], st.data());
-            });
-        if (hs == HG_OK)
-            hs = hg::gpu_build_neighbors(G->kind, (int64_t)G->child.size(), (int64_t)G->leaf_node.size(),
-                                         G->lvl.data(), G->idx.data(), G->child.data(), G->leaf.data(),
-                                         G->leaf_node.data(), stream, G->nbr_off, G->nbr_id);
+        hg::GpuTree T;
+        hs = hg::gpu_build_tree(M.view(), P, stream, T);
+        if (hs != HG_OK) return hs;
+        G->kind = P.kind;
+        G->lvl = std::move(T.lvl);
+        G->idx = std::move(T.idx);
+        G->child = std::move(T.child);
+        G->leaf = std::move(T.leaf);
+        G->lo = std::move(T.lo);
+        G->hi = std::move(T.hi);
+        G->rho = std::move(T.rho);
+        G->mass = std::move(T.mass);
+        G->delta = std::move(T.delta);
+        G->tau = std::move(T.tau);
+        G->q = std::move(T.q);
+        G->leaf_rho = std::move(T.leaf_rho);
+        G->leaf_node = std::move(T.leaf_node);
+        G->nbr_off = std::move(T.nbr_off);
+        G->nbr_id = std::move(T.nbr_id);
     } catch (const std::bad_alloc &) {
         hg::set_error("hg_build_grid_gpu: out of host memory");
-        hs = HG_ENOMEM;
+        return HG_ENOMEM;
     }
-    hg::gpu_eval_free(E);
-    if (hs != HG_OK) return hs;
     *out = G.release();
     return HG_OK;
 }

@@ -1,6 +1,5 @@
-// The tree construction's device parts (gbuild.cu), called by the builder in
-// build.cpp: the Monte Carlo node evaluation of one level of the node list,
-// and the neighbor lists of a finished node list (host arrays in and out).
+// The tree construction on the device (gbuild.cu), called by the builder in
+// build.cpp.
 #pragma once
 
 #include <cstdint>
@@ -10,18 +9,21 @@
 
 namespace hg {
 struct ModelView;
-struct NodeStats;
-struct GpuNodeEval;
-hg_status gpu_eval_create(const ModelView &host_model, hg_stream stream, GpuNodeEval **out);
-hg_status gpu_eval_level(GpuNodeEval *E, const hg_build_params &P, int64_t n, const int32_t *lvl, const int64_t *idx,
-                         NodeStats *out);
-void gpu_eval_free(GpuNodeEval *E);
 
-// Neighbor lists of every leaf wall (walls -x, +x, -y, +y, -z, +z), as the
-// host builder defines them: the leaves across the wall overlapping it with
-// positive area, sorted by decreasing overlap area, ties by ascending leaf
-// id.  lvl, idx: [3 n_nodes]; child, leaf: [n_nodes]; leaf_node: [n_leaves].
-hg_status gpu_build_neighbors(int32_t kind, int64_t n_nodes, int64_t n_leaves, const int32_t *lvl,
-                              const int64_t *idx, const int32_t *child, const int32_t *leaf, const int64_t *leaf_node,
-                              hg_stream stream, std::vector<int64_t> &nbr_off, std::vector<int32_t> &nbr_id);
+// A node list as the host builder stores it (per node: levels and indices
+// [3], bounds [3], first child or -1, leaf id or -1, statistics; per leaf:
+// its node and density; neighbor lists in CSR over the 6 walls of each leaf).
+struct GpuTree {
+    std::vector<int32_t> lvl, child, leaf, nbr_id;
+    std::vector<int64_t> idx, leaf_node, nbr_off;
+    std::vector<double> lo, hi, rho, mass, delta, tau, q, leaf_rho;
+};
+
+// The whole construction on the device: per level of the breadth-first node
+// list, the Monte Carlo node evaluation (one thread per node), a scan of the
+// child counts and the children appended in parent order; then the leaf
+// numbering, the bounds and the neighbor lists; one copy to the host at the
+// end.  The same node list as the host builder's level loop.
+hg_status gpu_build_tree(const ModelView &host_model, const hg_build_params &P, hg_stream stream, GpuTree &out);
+
 }  // namespace hg
