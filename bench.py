@@ -31,6 +31,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -111,7 +112,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the samples go to HG_CLOCKS_DIR when set (to keep them), else to a temporary folder
+        out_dir = os.environ.get("HG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"hg_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
