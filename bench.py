@@ -242,7 +242,7 @@ def matched_kd(hg, model, grids, P, PA, PK, PL, RT, TT):
     for _ in range(12):
         dm = math.exp(0.5 * (lo + hi))
         _, bpi, _, _ = synth.workload_disk_1e6(1, delta_max=dm)
-        H = hg.build_grid(model, bpi)
+        H = hg.build_grid_gpu(model, bpi)
         r = H.n_leaves / target
         if best is None or abs(r - 1) < abs(best[2] - 1):
             best = (dm, H, r)
@@ -261,6 +261,30 @@ def matched_kd(hg, model, grids, P, PA, PK, PL, RT, TT):
     return dict(delta_max=dm, leaves=H.n_leaves, leaves_over_octree=round(r, 4),
                 delta_rho=float(drho[2].item()), delta_tau=float(dtau[2].item()),
                 search_s=round(time.time() - t0, 1))
+
+
+def kd_orientations(hg, torch, model, O, K, P, PA, PK, PL, RT, TT, flush, stream):
+    """The disk k-d tree at the step's mass threshold split on the cyclic axis and on the axis of the
+    strongest density gradient (Sect. 2.2): leaves, Delta-rho and Delta-tau on the step's points and
+    paths, and an optical-depth walk of the step's rays (median of 5, L2 flushed), outside the timed step."""
+    res = {}
+    for name, axis in (("cyclic", 0), ("gradient", 1)):
+        _, bp, _, _ = synth.workload_disk_1e6(1)
+        bp.split_axis = axis
+        H = hg.build_grid_gpu(model, bp)
+        G = hg.load_grid(H)
+        _, rg = hg.sample_density(G, P)
+        ptau, _, _ = hg.trace_rays(G, PA, PK, PL, kappa=1.0, precision="fp64")
+        drho = hg.diff_stats(RT, rg)
+        dtau = hg.diff_stats(TT, ptau)
+        R = hg.prepare_rays(G, O, K)
+        tau, nc, st = R.trace()
+        ms = statistics.median(_timed_steps(torch, stream, 5, flush, lambda: R.trace(out=(tau, nc, st))))
+        cr = int(nc.sum().item())
+        R.free()
+        res[name] = dict(leaves=H.n_leaves, delta_rho=float(drho[2].item()), delta_tau=float(dtau[2].item()),
+                         walk_ms=ms, mean_ncross=cr / nc.numel(), gcross_per_s=cr / ms / 1e6)
+    return res
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -473,6 +497,9 @@ def run_ours(args):
     matched = None
     if world == 1 and not args.no_matched and args.workload == "disk-1e6":
         matched = matched_kd(hg, model, grids, P, PA, PK, PL, RT, TT)
+    orient = None
+    if world == 1 and args.kd_orientations and args.workload == "disk-1e6":
+        orient = kd_orientations(hg, torch, model, O, K, P, PA, PK, PL, RT, TT, flush, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -483,7 +510,8 @@ def run_ours(args):
                 dtype="f64" if prec == "fp64" else "f32+f64", data="synthetic",
                 config=dict(workload=args.workload, description=desc, rays_per_grid=n_rays, points=n_pts,
                             paths=n_paths, precision=prec, l2="flushed between steps (512 MB write)",
-                            grids=kern, kd_matched_to_octree=matched),
+                            grids=kern, kd_matched_to_octree=matched,
+                            **({"kd_orientations": orient} if orient else {})),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
                 clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
     if rank == 0:
@@ -1028,6 +1056,8 @@ def main(argv=None):
     ap.add_argument("--no-matched", action="store_true",
                     help="skip the k-d tree built to the octree's leaf count (quality at equal N_cells)")
     ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--kd-orientations", action="store_true",
+                    help="also compare the cyclic and gradient-axis k-d trees (quality and walk speed, untimed)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

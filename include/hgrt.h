@@ -91,7 +91,19 @@ typedef struct hg_model {
  * M = V * mean of rho_t at n_ran positions drawn uniformly in the node
  * (Eq. 1) with SplitMix64 keyed by the node's box, so that a node's samples
  * do not depend on the build order.  max_level counts octree levels; a k-d
- * tree may be 3*max_level splits deep (Sect. 2.1). */
+ * tree may be 3*max_level splits deep (Sect. 2.1).
+ * k-d split orientation (Sect. 2.2): HG_AXIS_CYCLIC, the axes in turn x, y,
+ * z, x, ...; or HG_AXIS_GRADIENT, the axis of the strongest density
+ * gradient in the node, estimated from its n_ran draws: on each axis a the
+ * draws below and above the node's midpoint give mean densities m_lo, m_hi,
+ * and g_a = |m_hi - m_lo| / (hi_a - lo_a) (0 when a half has no draw);
+ * among the axes halved fewer than max_level times (so that no axis is
+ * refined beyond the octree-equivalent level and the depth stays at most
+ * 3*max_level) the largest positive g_a wins, ties to the lower axis; when
+ * none is positive, the first of those axes in cyclic order from the
+ * node's depth mod 3.  Either way the split is at the midpoint. */
+#define HG_AXIS_CYCLIC 0
+#define HG_AXIS_GRADIENT 1
 typedef struct hg_build_params {
     int32_t kind; /* HG_OCTREE or HG_KDTREE */
     int32_t use_delta, use_tau, use_q;
@@ -100,6 +112,8 @@ typedef struct hg_build_params {
     int32_t n_ran;     /* >= 1 */
     uint64_t seed;
     int64_t max_nodes; /* 0 = unlimited; otherwise the build fails with HG_EOVERFLOW beyond it */
+    int32_t split_axis; /* k-d trees: HG_AXIS_CYCLIC or HG_AXIS_GRADIENT; ignored for octrees */
+    int32_t reserved;   /* 0 */
 } hg_build_params;
 
 /* Flat description of a grid: the node list of Sect. 2.2 (root first,

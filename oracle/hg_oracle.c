@@ -17,7 +17,8 @@
  *     optical depth of Eq. 2 against tau_max (Sect. 4.1) and the density
  *     dispersion q of Eq. 3 against q_max (Sect. 4.2); octree nodes split
  *     at the geometric centre into 8, k-d nodes at the geometric centre on
- *     the cyclic axis x, y, z, x, ... (Sect. 2.2);
+ *     the cyclic axis x, y, z, x, ... or on the axis of the strongest
+ *     density gradient estimated from the node's draws (Sect. 2.2);
  *   - top-down point location from the root (Sect. 2.3);
  *   - the path calculation: the ordered list of leaves whose interior a
  *     straight path crosses, with segment lengths, and the optical depth
@@ -85,6 +86,8 @@ typedef struct {
     int32_t max_level, n_ran;
     uint64_t seed;
     int64_t max_nodes;
+    int32_t split_axis; /* k-d: 0 cyclic, 1 strongest density gradient */
+    int32_t reserved;
 } or_params;
 
 typedef struct {
@@ -193,7 +196,35 @@ static double or_bound(const or_model *m, int a, int64_t i, int32_t l)
 typedef struct {
     double rho_mean, mass, delta, tau, q;
     int subdivide;
+    int axis; /* k-d: the axis a subdivision halves */
 } or_stats;
+
+/* The k-d split axis.  Cyclic: x, y, z, x, ... by depth (Sect. 2.2).
+ * Gradient (the paper's alternative orientation, Sect. 2.2): the axis with
+ * the strongest density gradient in the node, read from its draws: on axis
+ * a, m_lo and m_hi are the mean densities of the draws below and at or
+ * above the node's midpoint, g_a = |m_hi - m_lo| / (width on a), 0 when a
+ * half holds no draw.  Only axes halved fewer than max_level times compete
+ * (no axis finer than the octree-equivalent level); the largest positive
+ * g_a wins, the lower axis on ties; if none is positive, the first
+ * competing axis counting cyclically from depth mod 3. */
+static int or_split_axis(const or_params *P, const int32_t l[3], int32_t depth, const double g[3],
+                         const int has_both[3])
+{
+    int first = depth % 3;
+    if (P->split_axis == 0) return first;
+    int ax = first;
+    for (int k = 0; k < 3; k++) {
+        int b = (first + k) % 3;
+        if (l[b] < P->max_level) { ax = b; break; }
+    }
+    double best = 0.0;
+    for (int b = 0; b < 3; b++) {
+        if (l[b] >= P->max_level || !has_both[b]) continue;
+        if (g[b] > best) { best = g[b]; ax = b; }
+    }
+    return ax;
+}
 
 /* Sample a node, evaluate Eq. 1-3 and the stopping criteria. */
 static or_stats or_node_eval(const or_model *m, const or_params *P, const int32_t l[3], const int64_t i[3],
@@ -207,6 +238,10 @@ static or_stats or_node_eval(const or_model *m, const or_params *P, const int32_
     }
     uint64_t key = or_node_key(P->seed, l, i);
     double S = 0.0, rmin = 0.0, rmax = 0.0;
+    /* per axis: the sums of the draws' densities below and at or above the midpoint */
+    double half_mid[3], sum_below[3] = {0.0, 0.0, 0.0}, sum_above[3] = {0.0, 0.0, 0.0};
+    int32_t cnt_below[3] = {0, 0, 0};
+    for (int a = 0; a < 3; a++) half_mid[a] = or_bound(m, a, 2 * i[a] + 1, l[a] + 1);
     for (int32_t s = 0; s < P->n_ran; s++) {
         double x = lo[0] + or_uniform(key, 3ULL * s) * (hi[0] - lo[0]);
         double y = lo[1] + or_uniform(key, 3ULL * s + 1) * (hi[1] - lo[1]);
@@ -215,6 +250,11 @@ static or_stats or_node_eval(const or_model *m, const or_params *P, const int32_
         S += r;
         if (s == 0 || r < rmin) rmin = r;
         if (s == 0 || r > rmax) rmax = r;
+        double xyz[3] = {x, y, z};
+        for (int a = 0; a < 3; a++) {
+            if (xyz[a] < half_mid[a]) { sum_below[a] += r; cnt_below[a]++; }
+            else sum_above[a] += r;
+        }
     }
     double a = hi[0] - lo[0], b = hi[1] - lo[1], c = hi[2] - lo[2];
     double V = a * b * c;
@@ -229,6 +269,15 @@ static or_stats or_node_eval(const or_model *m, const or_params *P, const int32_
     if (P->use_tau && st.tau > P->tau_max) sub = 1;
     if (P->use_q && st.q > P->q_max) sub = 1;
     st.subdivide = at_max ? 0 : sub;
+    double g[3];
+    int has_both[3];
+    for (int a = 0; a < 3; a++) {
+        int32_t above = P->n_ran - cnt_below[a];
+        has_both[a] = cnt_below[a] > 0 && above > 0;
+        g[a] = has_both[a] ? fabs(sum_above[a] / (double)above - sum_below[a] / (double)cnt_below[a]) / (hi[a] - lo[a])
+                           : 0.0;
+    }
+    st.axis = (P->kind == OR_OCTREE) ? -1 : or_split_axis(P, l, depth, g, has_both);
     return st;
 }
 
@@ -332,7 +381,7 @@ int or_build(const or_model *m, const or_params *P, or_tree **out)
                     ic[a] = 2 * i[a] + ((c >> a) & 1);
                 }
             } else {
-                int a = depth % 3;
+                int a = st.axis;
                 lc[a] = l[a] + 1;
                 ic[a] = 2 * i[a] + c;
             }

@@ -223,6 +223,10 @@ hg_status check_build_args(const char *name, const hg_model *model, const hg_bui
         hg::set_error("%s: n_ran must be >= 1 and max_level in 0..20", name);
         return HG_EINVAL;
     }
+    if (P.split_axis != HG_AXIS_CYCLIC && P.split_axis != HG_AXIS_GRADIENT) {
+        hg::set_error("%s: split_axis must be HG_AXIS_CYCLIC or HG_AXIS_GRADIENT", name);
+        return HG_EINVAL;
+    }
     if (!(model->m_tot > 0.0)) { hg::set_error("%s: m_tot must be > 0", name); return HG_EINVAL; }
     if (model->kind < HG_MODEL_CONST || model->kind > HG_MODEL_DYADIC) {
         hg::set_error("%s: bad model kind %d", name, model->kind);
@@ -286,7 +290,7 @@ hg_status build_levels(const HostModel &M, const hg_build_params &P, hg_host_gri
             G.child[nd] = (int32_t)G.child.size();
             int32_t l[3] = {G.lvl[3 * nd], G.lvl[3 * nd + 1], G.lvl[3 * nd + 2]};
             int64_t i[3] = {G.idx[3 * nd], G.idx[3 * nd + 1], G.idx[3 * nd + 2]};
-            const int axis = (P.kind == HG_OCTREE) ? -1 : (l[0] + l[1] + l[2]) % 3;
+            const int axis = st[nd - begin].axis;  // k-d: the split axis (octree: -1)
             for (int c = 0; c < nch; c++) {
                 int32_t lc[3] = {l[0], l[1], l[2]};
                 int64_t ic[3] = {i[0], i[1], i[2]};

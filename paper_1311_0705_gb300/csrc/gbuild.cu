@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) child_count_kernel(int64_t begin, int64_t
 
 // Children of the level's nodes to subdivide, in parent order from `end`:
 // octree child c at (2 i_a + bit a of c) on every axis; k-d child c at
-// 2 i + c on the cyclic axis (l_x + l_y + l_z) mod 3.
+// 2 i + c on the node's split axis.
 __global__ void __launch_bounds__(256) append_kernel(int32_t kind, int64_t begin, int64_t end, int64_t m,
                                                      const NodeStats *__restrict__ st, const int64_t *__restrict__ off,
                                                      int32_t *lvl, int64_t *idx, int32_t *child) {
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) append_kernel(int32_t kind, int64_t begin
                     idx[3 * (first + c) + a] = 2 * i[a] + ((c >> a) & 1);
                 }
         } else {
-            const int axis = (l[0] + l[1] + l[2]) % 3;
+            const int axis = st[nd].axis;
             for (int c = 0; c < 2; c++)
                 for (int a = 0; a < 3; a++) {
                     lvl[3 * (first + c) + a] = a == axis ? l[a] + 1 : l[a];

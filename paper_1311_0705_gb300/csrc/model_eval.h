@@ -113,6 +113,7 @@ HG_HD double model_bound(const ModelView &m, int a, int64_t i, int32_t l) {
 struct NodeStats {
     double rho, mass, delta, tau, q;
     int32_t sub;
+    int32_t axis;  // k-d trees: the axis a subdivision splits (octrees: -1)
 };
 
 // The node with levels l and indices i (depth: its depth in the tree):
@@ -120,7 +121,12 @@ struct NodeStats {
 // M_tot (Eq. 1), tau = kappa M sqrt(a^2 + b^2 + c^2) / (abc) (Eq. 2) and
 // q = (rho_max - rho_min) / rho_max over the draws (Eq. 3); it is
 // subdivided when any enabled criterion exceeds its threshold, unless it is
-// at the maximum level.
+// at the maximum level.  A k-d node splits on the cyclic axis, or with
+// HG_AXIS_GRADIENT on the axis of the largest positive
+// g_a = |m_hi - m_lo| / (hi_a - lo_a), m_lo / m_hi the mean densities of the
+// draws below / at or above the node's midpoint on axis a (ties to the lower
+// axis), among the axes halved fewer than max_level times; when none has a
+// positive g_a, the first of those in cyclic order.
 HG_HD NodeStats eval_node_stats(const ModelView &M, const hg_build_params &P, const int32_t *l, const int64_t *i,
                                 int32_t depth) {
     double lo[3], hi[3];
@@ -129,6 +135,11 @@ HG_HD NodeStats eval_node_stats(const ModelView &M, const hg_build_params &P, co
         hi[a] = model_bound(M, a, i[a] + 1, l[a]);
     }
     const uint64_t key = box_key(P.seed, l, i);
+    const bool grad = (P.kind == HG_KDTREE && P.split_axis == HG_AXIS_GRADIENT);
+    double mid[3] = {0.0, 0.0, 0.0}, s_lo[3] = {0.0, 0.0, 0.0}, s_hi[3] = {0.0, 0.0, 0.0};
+    int32_t n_lo[3] = {0, 0, 0};
+    if (grad)
+        for (int a = 0; a < 3; a++) mid[a] = model_bound(M, a, 2 * i[a] + 1, l[a] + 1);
     double S = 0.0, rmin = 0.0, rmax = 0.0;
     for (int32_t s = 0; s < P.n_ran; s++) {
         double x = lo[0] + unit_draw(key, 3ULL * s) * (hi[0] - lo[0]);
@@ -138,6 +149,17 @@ HG_HD NodeStats eval_node_stats(const ModelView &M, const hg_build_params &P, co
         S += r;
         if (s == 0 || r < rmin) rmin = r;
         if (s == 0 || r > rmax) rmax = r;
+        if (grad) {
+            const double pos[3] = {x, y, z};
+            for (int a = 0; a < 3; a++) {
+                if (pos[a] < mid[a]) {
+                    s_lo[a] += r;
+                    n_lo[a]++;
+                } else {
+                    s_hi[a] += r;
+                }
+            }
+        }
     }
     NodeStats st;
     double a = hi[0] - lo[0], b = hi[1] - lo[1], c = hi[2] - lo[2];
@@ -151,6 +173,30 @@ HG_HD NodeStats eval_node_stats(const ModelView &M, const hg_build_params &P, co
     bool sub = (P.use_delta && st.delta > P.delta_max) || (P.use_tau && st.tau > P.tau_max) ||
                (P.use_q && st.q > P.q_max);
     st.sub = (sub && !at_max) ? 1 : 0;
+    st.axis = -1;
+    if (P.kind == HG_KDTREE) {
+        const int cyc = (l[0] + l[1] + l[2]) % 3;
+        st.axis = cyc;
+        if (grad) {
+            // every axis is halved at most max_level times (so the depth stays <= 3 max_level): the
+            // first such axis in cyclic order, unless an eligible axis has a positive gradient
+            for (int k = 0; k < 3; k++)
+                if (l[(cyc + k) % 3] < P.max_level) {
+                    st.axis = (cyc + k) % 3;
+                    break;
+                }
+            double best = 0.0;
+            for (int ax = 0; ax < 3; ax++) {
+                const int32_t n_hi = P.n_ran - n_lo[ax];
+                if (l[ax] >= P.max_level || n_lo[ax] == 0 || n_hi == 0) continue;
+                const double g = fabs(s_hi[ax] / (double)n_hi - s_lo[ax] / (double)n_lo[ax]) / (hi[ax] - lo[ax]);
+                if (g > best) {
+                    best = g;
+                    st.axis = ax;
+                }
+            }
+        }
+    }
     return st;
 }
 

@@ -169,7 +169,8 @@ class BuildParams:
 
     A criterion is disabled by ``use_*`` = False.  ``max_level`` is in octree
     levels; a k-d tree may go 3*max_level splits deep (one octree level equals
-    three k-d levels, Sect. 2.1).
+    three k-d levels, Sect. 2.1).  ``split_axis`` (k-d trees): 0 cycles through
+    x, y, z; 1 splits on the axis of the strongest density gradient (Sect. 2.2).
     """
 
     kind: int = TREE_OCTREE
@@ -183,6 +184,7 @@ class BuildParams:
     n_ran: int = 100
     kappa: float = 1.0
     seed: int = BASE_SEED
+    split_axis: int = 0
 
 
 # --------------------------------------------------------------------------- rays and points

@@ -60,6 +60,13 @@ CASES = [
     ("dyadic-oct", lambda: synth.make_dyadic(3, level=2), dict(kind=0, delta_max=1e-3, max_level=4)),
     ("const-tau", lambda: synth.make_const(2.0), dict(kind=1, use_delta=False, use_tau=True, tau_max=0.9,
                                                       max_level=6)),
+    # k-d trees split on the axis of the strongest density gradient (Sect. 2.2)
+    ("disk-kd-grad", lambda: synth.make_disk(), dict(kind=1, delta_max=5e-5, max_level=6, split_axis=1)),
+    ("torus-kd-grad", lambda: synth.make_torus(11, n_clumps=60), dict(kind=1, delta_max=1e-3, use_tau=True,
+                                                                      tau_max=2.0, use_q=True, q_max=0.9,
+                                                                      max_level=5, split_axis=1)),
+    ("dyadic-kd-grad", lambda: synth.make_dyadic(4, level=3), dict(kind=1, delta_max=2e-3, use_q=True,
+                                                                   q_max=0.5, max_level=5, split_axis=1)),
 ]
 
 
@@ -88,10 +95,10 @@ def _leaf_boxes(H):
     return H.node_lo[ln], H.node_hi[ln]
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_neighbor_lists_tile_walls_and_are_symmetric(kind):
+@pytest.mark.parametrize("kind,split_axis", [(0, 0), (1, 0), (1, 1)], ids=["octree", "kd", "kd-gradient"])
+def test_neighbor_lists_tile_walls_and_are_symmetric(kind, split_axis):
     model = synth.make_disk()
-    H = hg.build_grid(model, synth.BuildParams(kind=kind, delta_max=3e-4, max_level=6))
+    H = hg.build_grid(model, synth.BuildParams(kind=kind, delta_max=3e-4, max_level=6, split_axis=split_axis))
     lo, hi = _leaf_boxes(H)
     dlo, dhi = H.node_lo[0], H.node_hi[0]
     pairs = set()
@@ -163,6 +170,11 @@ def test_load_grid_rejects_corrupt_descriptions(small_host, what):
     desc = _corrupt(_desc(small_host), what)
     with pytest.raises(hg.HgError, match="grid description invalid"):
         hg.load_grid(desc, validate=True)
+
+
+def test_builder_rejects_bad_split_axis():
+    with pytest.raises(hg.HgError, match="split_axis"):
+        hg.build_grid(synth.make_disk(), synth.BuildParams(kind=1, delta_max=1e-3, max_level=3, split_axis=2))
 
 
 def test_builder_rejects_bad_parameters():

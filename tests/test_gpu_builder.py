@@ -53,6 +53,8 @@ EXACT = [
                                                       max_level=6)),
     ("torus-smooth-oct", lambda: synth.make_torus(13, n_clumps=0), dict(kind=0, delta_max=1e-3, use_q=True,
                                                                         q_max=0.5, max_level=5)),
+    ("dyadic-kd-grad", lambda: synth.make_dyadic(4, level=3), dict(kind=1, delta_max=2e-3, use_q=True, q_max=0.5,
+                                                                   max_level=5, split_axis=1)),
 ]
 WITH_EXP = [
     ("disk-oct", lambda: synth.make_disk(), dict(kind=0, delta_max=1e-4, max_level=6)),
@@ -60,6 +62,7 @@ WITH_EXP = [
     ("torus-kd-all", lambda: synth.make_torus(11, n_clumps=60), dict(kind=1, delta_max=1e-3, use_tau=True,
                                                                      tau_max=2.0, use_q=True, q_max=0.9,
                                                                      max_level=5)),
+    ("disk-kd-grad", lambda: synth.make_disk(), dict(kind=1, delta_max=5e-5, max_level=6, split_axis=1)),
 ]
 
 

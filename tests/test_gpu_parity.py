@@ -77,6 +77,22 @@ def disk_grids(hg):
     return model, out, o, k
 
 
+@pytest.mark.parametrize("shape", [dict(), dict(split="force"), dict(schedule=1, smem_nodes=0)],
+                         ids=["auto", "forced-split", "static-nosmem"])
+def test_gradient_axis_kd_sequences_bit_exact(hg, shape):
+    # a k-d tree split on the axis of the strongest density gradient (Sect. 2.2): nodes no longer cycle
+    # through x, y, z, so the descent, neighbor lists and segment planner meet uneven refinement
+    model, bp, n_rays, seed = synth.workload_disk_small()
+    bp.kind, bp.split_axis, bp.delta_max = synth.TREE_KD, 1, 5e-5
+    H = hg.build_grid(model, bp)
+    T = oracle.build_tree(model, bp)
+    np.testing.assert_array_equal(H.child_first, T.child)
+    assert (T.lvl.max(axis=0) == bp.max_level).all()
+    o, k = synth.emission_rays(seed + 7, 4000)
+    ref, _ = _compare(hg, hg.load_grid(H), T, o, k, **shape)
+    assert ref["ncross"].sum() > 4000 * 5
+
+
 SHAPES = [dict(), dict(schedule=1), dict(schedule=2, block=128, smem_nodes=0), dict(schedule=3, block=256, smem_nodes=64),
           dict(schedule=1, block=64, smem_nodes=100000), dict(min_blocks=4), dict(min_blocks=4, schedule=1, block=96)]
 

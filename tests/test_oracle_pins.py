@@ -101,6 +101,62 @@ def test_uniform_refinement_counts_and_octree_kd_equivalence(L):
     assert ko == kk
 
 
+def _layered(axis, level=2, low=1.0, high=10.0):
+    """Piecewise-constant model that varies along one axis only: `low` below the domain's middle on
+    that axis, `high` above (a dyadic lattice, x fastest in the table)."""
+    n = 1 << level
+    zz, yy, xx = np.indices((n, n, n))
+    upper = (xx, yy, zz)[axis] >= n // 2
+    vals = np.where(upper, high, low).astype(np.float64).reshape(-1)
+    lo, hi = np.full(3, -1.0), np.full(3, 1.0)
+    return synth.Model(synth.MODEL_DYADIC, np.array([float(level)], np.float64), vals.reshape(-1, 1),
+                       float(vals.sum()) * float(np.prod((hi - lo) / n)), lo, hi, "layered")
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_gradient_axis_splits_across_the_density_jump(axis):
+    # density constant on each side of the plane through the middle of `axis` (Sect. 2.2, the
+    # orientation of the strongest gradient): the root is halved on that axis; the cyclic rule
+    # halves it on x whatever the density
+    m = _layered(axis)
+    tg = oracle.build_tree(m, _bp(kind=synth.TREE_KD, delta_max=0.1, max_level=3, split_axis=1))
+    tc = oracle.build_tree(m, _bp(kind=synth.TREE_KD, delta_max=0.1, max_level=3, split_axis=0))
+    want = [0, 0, 0]
+    want[axis] = 1
+    assert tg.lvl[tg.child[0]].tolist() == want
+    assert tc.lvl[tc.child[0]].tolist() == [1, 0, 0]
+    # each half is uniform: no positive gradient below the root, so the halves split cyclically
+    c = tg.child[0]
+    for h in (c, c + 1):
+        if tg.child[h] >= 0:
+            depth = int(tg.lvl[h].sum())
+            grand = tg.lvl[tg.child[h]] - tg.lvl[h]
+            assert grand.tolist() == [1 if a == depth % 3 else 0 for a in range(3)] or tg.lvl[h][depth % 3] >= 3
+
+
+def test_gradient_axis_on_uniform_density_is_the_cyclic_tree():
+    m = synth.make_const(2.0)
+    kw = dict(kind=synth.TREE_KD, use_delta=False, use_tau=True, tau_max=0.9, max_level=4)
+    tg = oracle.build_tree(m, _bp(split_axis=1, **kw))
+    tc = oracle.build_tree(m, _bp(split_axis=0, **kw))
+    np.testing.assert_array_equal(tg.lvl, tc.lvl)
+    np.testing.assert_array_equal(tg.idx, tc.idx)
+    np.testing.assert_array_equal(tg.child, tc.child)
+
+
+def test_gradient_axis_halves_no_axis_beyond_max_level():
+    # always subdivide, max level 1: every axis is halved exactly once, so the leaves are the 2x2x2
+    # lattice although the density only varies along y
+    m = _layered(1, level=1)
+    t = oracle.build_tree(m, _bp(kind=synth.TREE_KD, delta_max=-1.0, max_level=1, split_axis=1))
+    assert t.n_leaves == 8
+    assert t.lvl.max(axis=0).tolist() == [1, 1, 1]
+    boxes = sorted(map(tuple, np.hstack([t.leaf_lo, t.leaf_hi])))
+    lattice = sorted((x, y, z, x + 1.0, y + 1.0, z + 1.0) for x in (-1.0, 0.0) for y in (-1.0, 0.0)
+                     for z in (-1.0, 0.0))
+    assert boxes == lattice
+
+
 def test_mass_criterion_exact_on_uniform_model():
     # uniform density: delta = V/V_dom exactly, so delta_max = 1/64 stops at 64 leaves
     m = synth.make_const(3.0)
