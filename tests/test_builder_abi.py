@@ -1,6 +1,7 @@
 """Host-side checks of the library (no GPU): exported C ABI, tree builder
 against the oracle's node list, neighbor-list invariants, and rejection of
 malformed grid descriptions by hg_load_grid's validation."""
+import math
 import os
 import re
 
@@ -212,3 +213,16 @@ def test_tau_max_recipe_matches_oracle(kind):
     assert above <= int(0.1 * H.n_leaves) + 1 and (taus >= tm).sum() >= H.n_leaves - int(0.9 * H.n_leaves)
     with pytest.raises(hg.HgError):
         hg.tau_max_recipe(model, bp, fraction=1.5)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_tau_max_recipe_known_quantile_matches_oracle(kind):
+    # the lattice whose Sect. 4.1 quantile the oracle pins (sorted cell values 1 x 56, 2, 4, 8 x 6):
+    # the library's recipe gives the same optical depth at every fraction
+    vals = np.array([1.0] * 56 + [2.0, 4.0] + [8.0] * 6)[np.random.default_rng(11).permutation(64)]
+    m = synth.Model(synth.MODEL_DYADIC, np.array([2.0]), vals.reshape(-1, 1), float(vals.sum()) * 0.125,
+                    np.full(3, -1.0), np.full(3, 1.0), "quantile lattice")
+    bp = synth.BuildParams(kind=kind, delta_max=1e-12, max_level=2, kappa=1.5)
+    for frac in (0.9, 0.89, 0.92, 0.0, 1.0):
+        assert hg.tau_max_recipe(m, bp, fraction=frac, threads=2) == oracle.tau_max_recipe(m, bp, fraction=frac)
+    assert hg.tau_max_recipe(m, bp) == pytest.approx(4.0 * 1.5 * math.sqrt(3.0) * 0.5, rel=4e-16)

@@ -5,6 +5,7 @@ mathematics fixes (exact integrals, exact volumes, leaf counts of uniform
 refinement), a published generator output, or a brute-force search that
 shares no logic with the oracle's descent and walk.
 """
+import dataclasses
 import json
 import math
 import os
@@ -191,6 +192,33 @@ def test_tau_criterion_uniform_count():
     t = oracle.build_tree(m, _bp(kind=synth.TREE_OCTREE, use_delta=False, use_tau=True, tau_max=tau_max,
                                  max_level=10))
     assert t.n_leaves == 8 ** L
+
+
+def _quantile_lattice_model():
+    # a level-2 lattice (64 cells of side 0.5) whose sorted values are 1 x 56, 2, 4, 8 x 6, placed by a
+    # fixed permutation; powers of two make every leaf's Monte Carlo mean exact (Eq. 1)
+    vals = np.array([1.0] * 56 + [2.0, 4.0] + [8.0] * 6)
+    vals = vals[np.random.default_rng(11).permutation(64)]
+    lo, hi = np.full(3, -1.0), np.full(3, 1.0)
+    return synth.Model(synth.MODEL_DYADIC, np.array([2.0]), vals.reshape(-1, 1), float(vals.sum()) * 0.125,
+                       lo, hi, "quantile lattice")
+
+
+@pytest.mark.parametrize("kind", [synth.TREE_OCTREE, synth.TREE_KD])
+def test_tau_max_recipe_known_quantile(kind):
+    # Sect. 4.1: tau_max is the leaf optical depth at sorted position floor(0.9 N).  With no effective mass
+    # threshold every node splits down to max level 2, giving the 64 lattice cells as leaves (k-d: depth 6);
+    # each leaf's Eq. 2 depth is kappa v sqrt(3) s with s = 1/2.  N = 64, so position floor(57.6) = 57 holds
+    # v = 4; positions 56 and 58 hold 2 and 8, so an off-by-one, a ceiling or rounding fails.
+    m = _quantile_lattice_model()
+    kappa = 1.5
+    bp = _bp(kind=kind, delta_max=1e-12, max_level=2, kappa=kappa, use_tau=True, tau_max=1e9)
+    t = oracle.build_tree(m, dataclasses.replace(bp, use_tau=False))
+    assert t.n_leaves == 64
+    unit = kappa * math.sqrt(3.0) * 0.5
+    # fraction -> value at position floor(fraction * 64) (clamped to 63)
+    for frac, v in ((0.9, 4.0), (0.89, 2.0), (0.875, 2.0), (0.92, 8.0), (0.0, 1.0), (1.0, 8.0), (0.5, 1.0)):
+        assert oracle.tau_max_recipe(m, bp, fraction=frac) == pytest.approx(v * unit, rel=4e-16), frac
 
 
 def test_density_dispersion_limits():
