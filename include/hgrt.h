@@ -192,7 +192,13 @@ typedef struct hg_grid_info {
     double lo[3], hi[3];
 } hg_grid_info;
 
-/* Upload a grid.  With validate != 0 the description is checked first
+/* Upload a grid: the node list of Sect. 2.2 and the six per-leaf neighbor
+ * lists of Sect. 2.3 (built once with the grid, sorted by decreasing overlap
+ * area) become 96-byte leaf records holding each wall's list head, the list
+ * tails and the descent nodes of the top-down search (Sect. 2.3), in device
+ * memory owned by the returned handle until hg_free_grid.  desc and the
+ * arrays it points to are host memory, read during the call only.  With
+ * validate != 0 the description is checked first
  * (links in range, children tiling their parent, leaf ids, every neighbor
  * list adjacent to its wall and tiling it); a failure returns HG_EFORMAT.
  * Needs a current CUDA device. */
@@ -271,10 +277,14 @@ hg_status hg_trace_rays_rho(const hg_grid *g, int64_t n, const double *o, const 
  * memory at the time they trace -- code running inside a stream capture
  * whose owner forbids allocation nodes, real-time loops that must never
  * enter an allocator, hosts that give the library a fixed memory budget.
- * This call computes exactly what hg_trace_rays computes (same arguments,
- * same results), but takes its scratch -- one 48-byte start record per ray
- * and a work counter -- from a fixed array compiled into the library, and
- * calls no cudaMalloc, cudaFree or other allocator.
+ * This call takes the arguments of hg_trace_rays and gives the same crossing
+ * counts and statuses; tau is the same sum, equal up to the grouping of the
+ * additions where hg_trace_rays cuts a long path into segments (a few ulps).
+ * It walks every path whole, each thread taking rays at a static stride,
+ * whatever opts.schedule and opts.split ask for (they are accepted and
+ * checked, then ignored).  Its scratch -- one 48-byte start record per ray
+ * and a work counter -- comes from a fixed array compiled into the library;
+ * it calls no cudaMalloc, cudaFree or other allocator.
  *   - n must not exceed HG_NOALLOC_MAX_RAYS; a larger n returns HG_EINVAL
  *     before anything is launched (split the batch, or use hg_trace_rays).
  *   - Every GPU that loads the library holds the array (about 12.6 MB)
@@ -329,7 +339,11 @@ hg_status hg_find_interactions(const hg_grid *g, int64_t n, const double *o, con
 hg_status hg_sample_density(const hg_grid *g, int64_t n, const double *pts, int32_t *cell, double *rho,
                             hg_stream stream);
 
-/* Adjoint of tau with respect to the leaf densities: for L = sum_r w_r tau_r,
+/* Adjoint of tau with respect to the leaf densities.  Sect. 3.2 defines the
+ * optical depth along a path as kappa times the integral of the density,
+ * which on a grid is tau_r = kappa sum over the path's segments of
+ * rho_cell ds (Sect. 2.3); tau is therefore linear in the leaf densities and
+ * this is its exact derivative: for L = sum_r w_r tau_r,
  * grad_rho[c] += kappa * sum over segments s of ray r inside c of w_r ds_s.
  * w dev f32[n]; grad_rho dev f32[n_leaves] (grad_precision 1, FP32 atomics)
  * or f64[n_leaves] (grad_precision 0, FP64 atomics), ACCUMULATED. */
@@ -431,7 +445,10 @@ hg_status hg_diff_stats(int64_t n, const double *a, const double *b, double *out
 hg_status hg_sum_i32(int64_t n, const int32_t *x, int64_t *out, hg_stream stream);
 
 /* ------------------------------------------------------------------------ batched launch
- * Many grids of uneven size, each with its own ray range, traced in one
+ * The paper traces paths through one grid at a time (Sect. 2.3); this
+ * batched form is this library's own: the optical-depth pass of
+ * hg_trace_rays (same contract and results, whole paths, never split) over
+ * many grids of uneven size, each with its own ray range, traced in one
  * persistent launch: ray chunks of every grid form one work list that
  * resident blocks drain through an atomic counter, larger grids first.
  * ray_begin (host i64[n_grids+1]) splits the concatenated ray and output

@@ -1791,13 +1791,17 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
     KernelFn k = pick_kernel(g->d.kind, MODE_TAU, prec, min_blocks);
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
     const size_t smem = (size_t)smem_nodes * node_bytes;
+    cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return cuda_err(e, "shared-memory limit of the allocation-free walk");
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
     if (e != cudaSuccess) return cuda_err(e, "occupancy query");
     if (per_sm < 1) {
         set_error("launch shape does not fit on an SM (block %d, %zu B shared)", block, smem);

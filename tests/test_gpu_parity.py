@@ -626,6 +626,66 @@ def test_batch_matches_single_grid_launches(hg):
             np.testing.assert_array_equal(_np(st[s]), _np(s1))
 
 
+def _uneven_batch(hg):
+    """Seven grids of uneven size for the batched launch: octree and k-d tree of each of the disk,
+    the clump-free ring and the ring with clumps (seeded parameters), one more disk octree, and one
+    grid that gets no rays; ray counts from 0 to ~2e4."""
+    rng = np.random.default_rng(synth.config_seed(4) + 101)
+    specs = []
+    for kind in (synth.TREE_OCTREE, synth.TREE_KD):
+        for mk in ("disk", "ring", "clumps"):
+            specs.append((kind, mk))
+    specs.append((synth.TREE_OCTREE, "disk"))
+    grids, trees, begins = [], [], [0]
+    n_rays = [int(x) for x in np.exp(rng.uniform(np.log(800), np.log(20000), len(specs)))]
+    n_rays[3] = 0
+    for (kind, mk), nr in zip(specs, n_rays):
+        sub = int(rng.integers(0, 2 ** 31))
+        if mk == "disk":
+            model = synth.make_disk(h_R=float(rng.uniform(0.15, 0.35)), h_z=float(rng.uniform(0.02, 0.08)))
+        elif mk == "ring":
+            model = synth.make_torus(sub, n_clumps=0, R0=float(rng.uniform(0.4, 0.6)), r_tube=0.15,
+                                     tau_eq=float(rng.uniform(1.0, 10.0)))
+        else:
+            model = synth.make_torus(sub, n_clumps=int(rng.integers(50, 300)), R0=0.5, r_tube=0.2,
+                                     tau_eq=float(rng.uniform(1.0, 10.0)))
+        target = float(np.exp(rng.uniform(np.log(2e3), np.log(4e4))))
+        bp = synth.BuildParams(kind=kind, delta_max=1.0 / target, max_level=7, seed=sub)
+        H = hg.build_grid(model, bp)
+        grids.append(hg.load_grid(H))
+        trees.append(oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho))
+        begins.append(begins[-1] + nr)
+    return grids, trees, begins
+
+
+def test_batch_matches_oracle_on_uneven_grids(hg):
+    # the batched persistent launch against the oracle, grid by grid: counts and statuses bit-exact, tau
+    # within 1e-6 (FP64) and 1e-5 (FP32-Kahan) of the oracle's FP64 sums; once from inside the domain to
+    # its exit, once along paths with both ends drawn in the domain (s_max)
+    grids, trees, begins = _uneven_batch(hg)
+    leaves = [g.n_leaves for g in grids]
+    assert max(leaves) > 4 * min(leaves)
+    n = begins[-1]
+    o, k = synth.emission_rays(synth.config_seed(4) + 5, n)
+    a, d, L = synth.endpoint_paths(synth.config_seed(4) + 6, n)
+    b = hg.Batch(grids, begins)
+    for rays in ((o, k, None), (a, d, L)):
+        O, K = _cuda(rays[0]), _cuda(rays[1])
+        S = None if rays[2] is None else _cuda(rays[2])
+        refs = [oracle.trace(t, rays[0][begins[i]:begins[i + 1]], rays[1][begins[i]:begins[i + 1]],
+                             smax=None if rays[2] is None else rays[2][begins[i]:begins[i + 1]], kappa=1.4)
+                for i, t in enumerate(trees)]
+        for prec, rtol in (("fp64", TAU_RTOL_FP64), ("fp32k", TAU_RTOL_FP32K)):
+            tau, nc, st = b.trace(O, K, S, kappa=1.4, precision=prec)
+            torch.cuda.synchronize()
+            for i, ref in enumerate(refs):
+                s = slice(begins[i], begins[i + 1])
+                np.testing.assert_array_equal(_np(nc[s]), ref["ncross"])
+                np.testing.assert_array_equal(_np(st[s]), ref["status"])
+                _check_tau(_np(tau[s]), ref["tau"], rtol)
+            assert int(_np(nc).sum()) > 0
+
+
 def test_batch_graph_capture_replay(hg):
     specs = synth.batch_specs(n_grids=3, rays_lo=1e3, rays_hi=5e3, leaves_lo=2e3, leaves_hi=1e4)
     grids, os_, ks, begins = [], [], [], [0]
@@ -746,53 +806,68 @@ def test_torus_full_size_builder_decisions_sampled(hg, torus_full):
         assert sp[0] == 1.0                      # and it would split the parent
 
 
-def test_torus_full_size_sequences_sampled(hg, torus_full):
+@pytest.fixture(scope="module")
+def torus_tree(torus_full):
+    model, bp, H, seed = torus_full
+    return oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho)
+
+
+def test_torus_full_size_1e6_rays_match_oracle(hg, torus_full, torus_tree):
+    # the full grid, 1e6 rays: crossing counts and statuses bit-exact against the oracle, tau within 1e-6
+    # (FP64) and 1e-5 (FP32-Kahan with the FP64 wall test) of the oracle's FP64 tau, in the launch shape the
+    # benchmark uses (work-ordered queue, automatic path segments); full cell sequences on a sample
     model, bp, H, seed = torus_full
     grid = hg.load_grid(H)
-    tree = oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho)
-    o, k = synth.emission_rays(seed, 20000)
-    _compare(hg, grid, tree, o, k)
-    _compare(hg, grid, tree, o, k, precision="fp32k")
+    o, k = synth.emission_rays(seed, 1_000_000)
+    ref = oracle.trace(torus_tree, o, k)
+    O, K = _cuda(o), _cuda(k)
+    for prec, rtol in (("fp64", TAU_RTOL_FP64), ("fp32k", TAU_RTOL_FP32K)):
+        tau, nc, st = hg.trace_rays(grid, O, K, precision=prec)
+        np.testing.assert_array_equal(_np(nc), ref["ncross"])
+        np.testing.assert_array_equal(_np(st), ref["status"])
+        _check_tau(_np(tau), ref["tau"], rtol)
+    assert ref["ncross"].mean() > 20
+    sel = np.random.default_rng(3).choice(o.shape[0], 20000, replace=False)
+    _compare(hg, grid, torus_tree, o[sel], k[sel])
+    _compare(hg, grid, torus_tree, o[sel], k[sel], precision="fp32k")
 
 
-def test_torus_full_size_gradient(hg, torus_full):
-    # the adjoint at full size (1e7 rays, ~8.4e6 leaves): FP64 reductions against an FP64 accumulation of
-    # the emitted segments (whose cells and lengths match the oracle bit for bit in the tests above), FP32
-    # reductions within gamma_{n+1} of it per cell, and central differences on 100 cells
+def test_torus_full_size_gradient(hg, torus_full, torus_tree):
+    # the adjoint at full size (1e7 rays, the full k-d grid): FP64 and FP32 reductions on the GPU against
+    # the oracle's FP64 accumulation of its own emitted segments (in ten 1e6-ray chunks): FP64 within
+    # 2 (n_c + 10) u per cell (all terms positive, only the order differs: n_c atomic additions against n_c
+    # additions plus ten chunk sums), FP32 within gamma_{n_c + 1}; and central differences on 100 cells
     model, bp, H, seed = torus_full
     grid = hg.load_grid(H)
     n = 10_000_000
     o, k = synth.emission_rays(seed, n)
     w = synth.adjoint_weights(seed + 3, n)
     O, K, W = _cuda(o), _cuda(k), _cuda(w, torch.float32)
-    g64 = hg.tau_gradient(grid, O, K, W, grad_precision="fp64")
-    g32 = hg.tau_gradient(grid, O, K, W, grad_precision="fp32")
-    R = hg.prepare_rays(grid, O, K)
-    out = R.emit_single_pass()
-    nc = out["ncross"].long()
-    cell = out["seg_cell"].long()
-    ray_of_seg = torch.repeat_interleave(torch.arange(n, device="cuda"), nc)
-    terms = W.double()[ray_of_seg] * out["seg_ds"]
-    g_ref = torch.zeros(grid.n_leaves, dtype=torch.float64, device="cuda").index_add_(0, cell, terms)
-    counts = torch.bincount(cell, minlength=grid.n_leaves).double()
-    del ray_of_seg, terms, out
-    R.free()
-    # all terms are positive: two FP64 orders differ by at most n_c ulps relative
-    err64 = (g64 - g_ref).abs()
-    assert bool((err64 <= 2.3e-16 * (counts + 1) * g_ref + 1e-300).all()), float((err64 / g_ref.clamp_min(1e-300)).max())
+    g64 = _np(hg.tau_gradient(grid, O, K, W, grad_precision="fp64"))
+    g32 = _np(hg.tau_gradient(grid, O, K, W, grad_precision="fp32")).astype(np.float64)
+    g_ref = np.zeros(H.n_leaves, np.float64)
+    counts = np.zeros(H.n_leaves, np.int64)
+    chunk = 1_000_000
+    for a in range(0, n, chunk):
+        r = oracle.trace(torus_tree, o[a:a + chunk], k[a:a + chunk], emit=True)
+        g_ref += oracle.adjoint(H.n_leaves, r["seg_off"], r["seg_cell"], r["seg_ds"],
+                                w[a:a + chunk].astype(np.float64))
+        counts += np.bincount(r["seg_cell"], minlength=H.n_leaves)
+        del r
+    err64 = np.abs(g64 - g_ref)
+    assert (err64 <= 2.3e-16 * (counts + 10) * g_ref + 1e-300).all(), float((err64 / np.maximum(g_ref, 1e-300)).max())
     u = 2.0 ** -24
     gam = (counts + 1) * u / (1 - (counts + 1) * u)
-    err32 = (g32.double() - g_ref).abs()
-    assert bool((err32 <= gam * g_ref + 1e-30).all())
-    hit = torch.nonzero(g_ref > 0).squeeze(1)
-    rel32 = (err32[hit] / g_ref[hit])
-    assert float(rel32.median()) < 1e-6
+    err32 = np.abs(g32 - g_ref)
+    assert (err32 <= gam * g_ref + 1e-30).all()
+    hit = np.nonzero(g_ref > 0)[0]
+    assert hit.size > 100_000
+    assert float(np.median(err32[hit] / g_ref[hit])) < 1e-6
+    assert (g64[counts == 0] == 0).all() and (g32[counts == 0] == 0).all()
     # central differences: tau is linear in rho, and rays that miss the cell give identical bits both ways
     rng = np.random.default_rng(5)
-    gh = _np(g64)
-    hit_np = _np(hit)
-    pw = gh[hit_np] / gh[hit_np].sum()
-    cells = np.concatenate([rng.choice(hit_np, 50, replace=False), rng.choice(hit_np, 50, replace=False, p=pw)])
+    pw = g_ref[hit] / g_ref[hit].sum()
+    cells = np.concatenate([rng.choice(hit, 50, replace=False), rng.choice(hit, 50, replace=False, p=pw)])
     rho = torch.tensor(H.leaf_rho, dtype=torch.float64, device="cuda")
     Wd = W.double()
     for c in cells:
@@ -803,4 +878,4 @@ def test_torus_full_size_gradient(hg, torus_full):
         tp, _ = hg.trace_rays_rho(grid, O, K, rp)
         tm, _ = hg.trace_rays_rho(grid, O, K, rm)
         fd = float((Wd * (tp - tm)).sum()) / (2 * h)
-        assert fd == pytest.approx(gh[c], rel=1e-6)
+        assert fd == pytest.approx(g_ref[c], rel=1e-6)
