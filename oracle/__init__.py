@@ -58,7 +58,7 @@ class _Params(C.Structure):
                 ("delta_max", C.c_double), ("tau_max", C.c_double), ("q_max", C.c_double),
                 ("kappa", C.c_double), ("max_level", C.c_int32), ("n_ran", C.c_int32),
                 ("seed", C.c_uint64), ("max_nodes", C.c_int64), ("split_axis", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("split_plane", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -146,6 +146,7 @@ def _params(bp) -> _Params:
     p.seed = int(bp.seed) & ((1 << 64) - 1)
     p.max_nodes = int(getattr(bp, "max_nodes", 0) or 0)
     p.split_axis = int(getattr(bp, "split_axis", 0) or 0)
+    p.split_plane = int(getattr(bp, "split_plane", 0) or 0)
     return p
 
 

@@ -16,9 +16,12 @@
  *     fraction criterion delta > delta_max (Sect. 2.2 and 4.1), the node
  *     optical depth of Eq. 2 against tau_max (Sect. 4.1) and the density
  *     dispersion q of Eq. 3 against q_max (Sect. 4.2); octree nodes split
- *     at the geometric centre into 8, k-d nodes at the geometric centre on
- *     the cyclic axis x, y, z, x, ... or on the axis of the strongest
- *     density gradient estimated from the node's draws (Sect. 2.2);
+ *     into 8 at the geometric centre or at the barycentre of their draws,
+ *     k-d nodes on the cyclic axis x, y, z, x, ... or on the axis of the
+ *     strongest density gradient estimated from the node's draws, at the
+ *     geometric centre, at the plane that gives both halves equal Monte
+ *     Carlo mass, or at the plane that gives them equal mean density
+ *     (Sect. 2.2's orientation and location options);
  *   - top-down point location from the root (Sect. 2.3);
  *   - the path calculation: the ordered list of leaves whose interior a
  *     straight path crosses, with segment lengths, and the optical depth
@@ -87,7 +90,7 @@ typedef struct {
     uint64_t seed;
     int64_t max_nodes;
     int32_t split_axis; /* k-d: 0 cyclic, 1 strongest density gradient */
-    int32_t reserved;
+    int32_t split_plane; /* 0 geometric centre; octree 1 barycentre; k-d 2 equal mass, 3 equal mean density */
 } or_params;
 
 typedef struct {
@@ -196,8 +199,116 @@ static double or_bound(const or_model *m, int a, int64_t i, int32_t l)
 typedef struct {
     double rho_mean, mass, delta, tau, q;
     int subdivide;
-    int axis; /* k-d: the axis a subdivision halves */
+    int axis;        /* k-d: the axis a subdivision splits */
+    double plane[3]; /* where the planes cut: octree all three axes, k-d the split axis */
 } or_stats;
+
+#define OR_PLANE_CENTRE 0
+#define OR_PLANE_BARYCENTRE 1
+#define OR_PLANE_EQUAL_MASS 2
+#define OR_PLANE_EQUAL_DENSITY 3
+
+/* One Monte Carlo draw of a node: its position and density. */
+typedef struct {
+    double x[3];
+    double r;
+    int32_t s; /* draw number */
+} or_draw;
+
+static int or_draw_axis; /* axis the comparison below orders by (set before each qsort) */
+
+static int or_cmp_draw(const void *pa, const void *pb)
+{
+    const or_draw *a = (const or_draw *)pa, *b = (const or_draw *)pb;
+    double u = a->x[or_draw_axis], v = b->x[or_draw_axis];
+    if (u < v) return -1;
+    if (u > v) return 1;
+    return (a->s > b->s) - (a->s < b->s);
+}
+
+/* The geometric centre of [lo, hi] on one axis of a node whose box is not a
+ * dyadic lattice cell. */
+static double or_centre(double lo, double hi) { return lo + 0.5 * (hi - lo); }
+
+/* Barycentric octree subdivision (Sect. 2.2, after the earlier octree paper):
+ * the three planes pass through the node's centre of mass, estimated from
+ * its draws as sum(rho x) / sum(rho), both sums in draw order.  An axis whose
+ * estimate is undefined (no mass) or not strictly inside the node is cut at
+ * the geometric centre. */
+static void or_barycentre(const or_draw *d, int32_t n, const double lo[3], const double hi[3], double c[3])
+{
+    double S = 0.0, Sx[3] = {0.0, 0.0, 0.0};
+    for (int32_t s = 0; s < n; s++) {
+        S += d[s].r;
+        for (int a = 0; a < 3; a++) Sx[a] += d[s].r * d[s].x[a];
+    }
+    for (int a = 0; a < 3; a++) {
+        double v = (S > 0.0) ? Sx[a] / S : or_centre(lo[a], hi[a]);
+        if (!(lo[a] < v && v < hi[a])) v = or_centre(lo[a], hi[a]);
+        c[a] = v;
+    }
+}
+
+/* k-d split location on axis a (Sect. 2.2).  The draws are ordered by their
+ * coordinate on a (ties by draw number); a plane between consecutive draws
+ * j and j+1 sits at x_j + (x_{j+1} - x_j) / 2.
+ *   equal mass: the first j at which the running sum of densities, left to
+ *     right, reaches half the total (2 C_j >= C_total), but never the last
+ *     draw -- the two sides then carry as equal Monte Carlo masses as the
+ *     draws allow;
+ *   equal mean density: the j minimising |C_j / (j+1) - R_j / (n-1-j)|, the
+ *     mean draw density left of the plane against right of it (R_j summed
+ *     right to left), over the j whose two draws differ in position; ties
+ *     go to the j nearest the middle (smallest |2j - (n-2)|), then the
+ *     smaller j.
+ * No usable draw pair, no mass (equal mass), or a plane not strictly inside
+ * the node: the geometric centre. */
+static double or_kd_plane(int mode, or_draw *d, int32_t n, int a, double lo, double hi)
+{
+    double fallback = or_centre(lo, hi);
+    if (n < 2) return fallback;
+    or_draw_axis = a;
+    qsort(d, (size_t)n, sizeof(or_draw), or_cmp_draw);
+    int32_t best = -1;
+    if (mode == OR_PLANE_EQUAL_MASS) {
+        double total = 0.0;
+        for (int32_t j = 0; j < n; j++) total += d[j].r;
+        if (!(total > 0.0)) return fallback;
+        double c = 0.0;
+        for (int32_t j = 0; j < n; j++) {
+            c += d[j].r;
+            if (2.0 * c >= total) { best = j; break; }
+        }
+        if (best == n - 1) best = n - 2;
+        if (best < 0 || !(d[best].x[a] < d[best + 1].x[a])) return fallback;
+    } else {
+        double *right = malloc((size_t)n * sizeof(double));
+        if (!right) return fallback;
+        double r = 0.0;
+        for (int32_t j = n - 1; j >= 1; j--) {
+            r += d[j].r;
+            right[j - 1] = r; /* sum of draws j .. n-1: the right side of plane j-1 */
+        }
+        double c = 0.0, best_d = 0.0;
+        int32_t best_mid = 0;
+        for (int32_t j = 0; j <= n - 2; j++) {
+            c += d[j].r;
+            if (!(d[j].x[a] < d[j + 1].x[a])) continue;
+            double diff = fabs(c / (double)(j + 1) - right[j] / (double)(n - 1 - j));
+            int32_t mid = abs(2 * j - (n - 2));
+            if (best < 0 || diff < best_d || (diff == best_d && mid < best_mid)) {
+                best = j;
+                best_d = diff;
+                best_mid = mid;
+            }
+        }
+        free(right);
+        if (best < 0) return fallback;
+    }
+    double v = d[best].x[a] + 0.5 * (d[best + 1].x[a] - d[best].x[a]);
+    return (lo < v && v < hi) ? v : fallback;
+}
+
 
 /* The k-d split axis.  Cyclic: x, y, z, x, ... by depth (Sect. 2.2).
  * Gradient (the paper's alternative orientation, Sect. 2.2): the axis with
@@ -226,27 +337,35 @@ static int or_split_axis(const or_params *P, const int32_t l[3], int32_t depth, 
     return ax;
 }
 
-/* Sample a node, evaluate Eq. 1-3 and the stopping criteria. */
+/* Sample a node (box [lo, hi], per-axis levels l and positions i, which key
+ * its draws), evaluate Eq. 1-3 and the stopping criteria, and for a node to
+ * subdivide the split axis (k-d) and plane position(s). */
 static or_stats or_node_eval(const or_model *m, const or_params *P, const int32_t l[3], const int64_t i[3],
-                             int32_t depth)
+                             int32_t depth, const double lo[3], const double hi[3])
 {
     or_stats st;
-    double lo[3], hi[3];
-    for (int a = 0; a < 3; a++) {
-        lo[a] = or_bound(m, a, i[a], l[a]);
-        hi[a] = or_bound(m, a, i[a] + 1, l[a]);
-    }
     uint64_t key = or_node_key(P->seed, l, i);
     double S = 0.0, rmin = 0.0, rmax = 0.0;
     /* per axis: the sums of the draws' densities below and at or above the midpoint */
     double half_mid[3], sum_below[3] = {0.0, 0.0, 0.0}, sum_above[3] = {0.0, 0.0, 0.0};
     int32_t cnt_below[3] = {0, 0, 0};
-    for (int a = 0; a < 3; a++) half_mid[a] = or_bound(m, a, 2 * i[a] + 1, l[a] + 1);
+    for (int a = 0; a < 3; a++)
+        half_mid[a] = (P->split_plane == OR_PLANE_CENTRE) ? or_bound(m, a, 2 * i[a] + 1, l[a] + 1)
+                                                          : or_centre(lo[a], hi[a]);
+    or_draw *draws = NULL;
+    if (P->split_plane != OR_PLANE_CENTRE) draws = malloc((size_t)P->n_ran * sizeof(or_draw));
     for (int32_t s = 0; s < P->n_ran; s++) {
         double x = lo[0] + or_uniform(key, 3ULL * s) * (hi[0] - lo[0]);
         double y = lo[1] + or_uniform(key, 3ULL * s + 1) * (hi[1] - lo[1]);
         double z = lo[2] + or_uniform(key, 3ULL * s + 2) * (hi[2] - lo[2]);
         double r = or_rho_true(m, x, y, z);
+        if (draws) {
+            draws[s].x[0] = x;
+            draws[s].x[1] = y;
+            draws[s].x[2] = z;
+            draws[s].r = r;
+            draws[s].s = s;
+        }
         S += r;
         if (s == 0 || r < rmin) rmin = r;
         if (s == 0 || r > rmax) rmax = r;
@@ -278,6 +397,22 @@ static or_stats or_node_eval(const or_model *m, const or_params *P, const int32_
                            : 0.0;
     }
     st.axis = (P->kind == OR_OCTREE) ? -1 : or_split_axis(P, l, depth, g, has_both);
+    for (int a = 0; a < 3; a++) st.plane[a] = or_bound(m, a, 2 * i[a] + 1, l[a] + 1);
+    if (P->split_plane != OR_PLANE_CENTRE) {
+        for (int a = 0; a < 3; a++) st.plane[a] = or_centre(lo[a], hi[a]);
+        if (draws && st.subdivide) {
+            if (P->kind == OR_OCTREE)
+                or_barycentre(draws, P->n_ran, lo, hi, st.plane);
+            else
+                st.plane[st.axis] = or_kd_plane(P->split_plane, draws, P->n_ran, st.axis, lo[st.axis], hi[st.axis]);
+        }
+        /* a box too thin to hold a plane strictly inside on a cut axis stays a leaf */
+        for (int a = 0; a < 3; a++) {
+            if (P->kind == OR_KD && a != st.axis) continue;
+            if (!(lo[a] < st.plane[a] && st.plane[a] < hi[a])) st.subdivide = 0;
+        }
+    }
+    free(draws);
     return st;
 }
 
@@ -287,7 +422,12 @@ void or_node_stats(const or_model *m, const or_params *P, const int32_t *l, cons
 {
     int32_t depth = l[0] + l[1] + l[2];
     if (P->kind == OR_OCTREE) depth = l[0];
-    or_stats st = or_node_eval(m, P, l, i, depth);
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = or_bound(m, a, i[a], l[a]);
+        hi[a] = or_bound(m, a, i[a] + 1, l[a]);
+    }
+    or_stats st = or_node_eval(m, P, l, i, depth, lo, hi);
     out[0] = st.subdivide;
     out[1] = st.rho_mean;
     out[2] = st.mass;
@@ -323,14 +463,17 @@ static int or_tree_reserve(or_tree *T, int64_t need)
     return 0;
 }
 
-static void or_push(or_tree *T, const or_model *m, const int32_t l[3], const int64_t i[3])
+/* Append a node: per-axis levels and positions, and its box (NULL: the
+ * dyadic lattice cell those give). */
+static void or_push(or_tree *T, const or_model *m, const int32_t l[3], const int64_t i[3], const double *lo,
+                    const double *hi)
 {
     int64_t n = T->n_nodes++;
     for (int a = 0; a < 3; a++) {
         T->lvl[3 * n + a] = l[a];
         T->idx[3 * n + a] = i[a];
-        T->lo[3 * n + a] = or_bound(m, a, i[a], l[a]);
-        T->hi[3 * n + a] = or_bound(m, a, i[a] + 1, l[a]);
+        T->lo[3 * n + a] = lo ? lo[a] : or_bound(m, a, i[a], l[a]);
+        T->hi[3 * n + a] = hi ? hi[a] : or_bound(m, a, i[a] + 1, l[a]);
     }
     T->child[n] = -1;
     T->leaf[n] = -1;
@@ -350,18 +493,23 @@ int or_build(const or_model *m, const or_params *P, or_tree **out)
 {
     *out = NULL;
     if (P->n_ran < 1 || !(m->m_tot > 0.0) || P->max_level < 0 || P->max_level > 20) return -3;
+    if (P->split_plane < 0 || P->split_plane > 3) return -3;
+    if (P->kind == OR_OCTREE && P->split_plane > OR_PLANE_BARYCENTRE) return -3;
+    if (P->kind == OR_KD && P->split_plane == OR_PLANE_BARYCENTRE) return -3;
     or_tree *T = calloc(1, sizeof(or_tree));
     if (!T) return -1;
     T->kind = P->kind;
     if (or_tree_reserve(T, 1)) { or_tree_free(T); return -1; }
     int32_t l0[3] = {0, 0, 0};
     int64_t i0[3] = {0, 0, 0};
-    or_push(T, m, l0, i0);
+    or_push(T, m, l0, i0, NULL, NULL);
     for (int64_t n = 0; n < T->n_nodes; n++) {
         int32_t l[3] = {T->lvl[3 * n], T->lvl[3 * n + 1], T->lvl[3 * n + 2]};
         int64_t i[3] = {T->idx[3 * n], T->idx[3 * n + 1], T->idx[3 * n + 2]};
+        double lo[3] = {T->lo[3 * n], T->lo[3 * n + 1], T->lo[3 * n + 2]};
+        double hi[3] = {T->hi[3 * n], T->hi[3 * n + 1], T->hi[3 * n + 2]};
         int32_t depth = (T->kind == OR_OCTREE) ? l[0] : l[0] + l[1] + l[2];
-        or_stats st = or_node_eval(m, P, l, i, depth);
+        or_stats st = or_node_eval(m, P, l, i, depth, lo, hi);
         T->rho[n] = st.rho_mean;
         T->mass[n] = st.mass;
         T->delta[n] = st.delta;
@@ -375,17 +523,22 @@ int or_build(const or_model *m, const or_params *P, or_tree **out)
         for (int c = 0; c < nch; c++) {
             int32_t lc[3] = {l[0], l[1], l[2]};
             int64_t ic[3] = {i[0], i[1], i[2]};
-            if (T->kind == OR_OCTREE) {
-                for (int a = 0; a < 3; a++) {
-                    lc[a] = l[a] + 1;
-                    ic[a] = 2 * i[a] + ((c >> a) & 1);
-                }
-            } else {
-                int a = st.axis;
+            double clo[3] = {lo[0], lo[1], lo[2]}, chi[3] = {hi[0], hi[1], hi[2]};
+            for (int a = 0; a < 3; a++) {
+                if (T->kind == OR_KD && a != st.axis) continue;
+                int up = (T->kind == OR_OCTREE) ? ((c >> a) & 1) : c;
                 lc[a] = l[a] + 1;
-                ic[a] = 2 * i[a] + c;
+                ic[a] = 2 * i[a] + up;
+                if (up)
+                    clo[a] = st.plane[a];
+                else
+                    chi[a] = st.plane[a];
             }
-            or_push(T, m, lc, ic);
+            /* centre planes: the child's dyadic cell (the same values, from its levels and positions) */
+            if (P->split_plane == OR_PLANE_CENTRE)
+                or_push(T, m, lc, ic, NULL, NULL);
+            else
+                or_push(T, m, lc, ic, clo, chi);
         }
     }
     /* leaves in list order */

@@ -35,6 +35,11 @@ MODEL_DYADIC = 3
 TREE_OCTREE = 0
 TREE_KD = 1
 
+PLANE_CENTRE = 0
+PLANE_BARYCENTRE = 1
+PLANE_EQUAL_MASS = 2
+PLANE_EQUAL_DENSITY = 3
+
 #: truncation radius of a clump in units of its sigma
 CLUMP_CUT_SIGMAS = 5.0
 
@@ -171,6 +176,9 @@ class BuildParams:
     levels; a k-d tree may go 3*max_level splits deep (one octree level equals
     three k-d levels, Sect. 2.1).  ``split_axis`` (k-d trees): 0 cycles through
     x, y, z; 1 splits on the axis of the strongest density gradient (Sect. 2.2).
+    ``split_plane``: 0 cuts at the geometric centre; octrees 1 at the
+    barycentre of the node's draws; k-d trees 2 at equal mass, 3 at equal
+    mean density of the two halves (Sect. 2.2's location options).
     """
 
     kind: int = TREE_OCTREE
@@ -185,6 +193,7 @@ class BuildParams:
     kappa: float = 1.0
     seed: int = BASE_SEED
     split_axis: int = 0
+    split_plane: int = 0
 
 
 # --------------------------------------------------------------------------- rays and points

@@ -569,3 +569,162 @@ def test_interaction_nonpositive_and_nan_tau(disk_small):
     assert (q["t"] == 0.0).all() and (q["ncross"] == 1).all()
     q2 = oracle.interact(t, o, k, np.full(n, np.nan))
     assert (q2["status"] == oracle.RAY_BADINPUT).all() and (q2["cell"] == -1).all()
+
+
+# ----------------------------------------------------------------------------- split locations (Sect. 2.2)
+# Non-dyadic planes: the barycentric octree and the equal-mass and equal-mean-density k-d trees.  The root's
+# planes are pinned against positions the model fixes analytically (the estimates come from n_ran draws,
+# hence the tolerances, about 5 standard deviations at 4000 draws); deeper trees against exact tiling,
+# brute-force location, brute-force sequences and the uniform-density closed form.
+
+def _slabs_x(values):
+    """Piecewise-constant model varying along x only: len(values) = 2^L slabs of equal width."""
+    n = len(values)
+    L = int(round(math.log2(n)))
+    zz, yy, xx = np.indices((n, n, n))
+    vals = np.asarray(values, np.float64)[xx].reshape(-1)
+    lo, hi = np.full(3, -1.0), np.full(3, 1.0)
+    return synth.Model(synth.MODEL_DYADIC, np.array([float(L)]), vals.reshape(-1, 1),
+                       float(vals.sum()) * float(np.prod((hi - lo) / n)), lo, hi, "slabs")
+
+
+def _root_planes(model, kind, plane, n_ran=4000):
+    t = oracle.build_tree(model, _bp(kind=kind, delta_max=1e-12, max_level=1, n_ran=n_ran, split_plane=plane))
+    c0 = t.child[0]
+    assert c0 > 0
+    return t.hi[c0]  # the lower child's upper corner holds the cut positions
+
+
+def test_barycentric_octree_root_at_centre_of_mass():
+    # rho = 1 for x < 0 and 3 for x >= 0: centre of mass ((1)(-1/2) + (3)(1/2)) / 4 = 1/4 on x, 0 on y and z
+    c = _root_planes(_slabs_x([1.0, 3.0]), synth.TREE_OCTREE, synth.PLANE_BARYCENTRE)
+    assert c[0] == pytest.approx(0.25, abs=0.05)
+    assert abs(c[1]) < 0.05 and abs(c[2]) < 0.05
+    # uniform density: the centre of mass is the geometric centre
+    c = _root_planes(synth.make_const(1.0), synth.TREE_OCTREE, synth.PLANE_BARYCENTRE)
+    assert np.abs(c).max() < 0.06
+
+
+def test_equal_mass_kd_root_halves_the_mass():
+    # rho = 1 for x < 0, 3 for x >= 0: total mass 4 (per unit y-z area / 4), half reached at 1 + 3c = 2, c = 1/3
+    c = _root_planes(_slabs_x([1.0, 3.0]), synth.TREE_KD, synth.PLANE_EQUAL_MASS)
+    assert c[0] == pytest.approx(1.0 / 3.0, abs=0.05)
+    assert c[1] == 1.0 and c[2] == 1.0   # the cyclic root cuts x only
+    # rho = 3 below 0, 1 above: mirror image, c = -1/3
+    c = _root_planes(_slabs_x([3.0, 1.0]), synth.TREE_KD, synth.PLANE_EQUAL_MASS)
+    assert c[0] == pytest.approx(-1.0 / 3.0, abs=0.05)
+    # uniform density: the median of the draws
+    c = _root_planes(synth.make_const(1.0), synth.TREE_KD, synth.PLANE_EQUAL_MASS)
+    assert abs(c[0]) < 0.06
+
+
+def test_equal_mean_density_kd_root():
+    # slabs of width 1/2 on x with rho 1, 1, 7, 1: left mean (1 + 7c) / (1 + c) equals right mean
+    # (4 - 7c) / (1 - c) only at c = 1/3 (left mean below the right one before it, above after it)
+    c = _root_planes(_slabs_x([1.0, 1.0, 7.0, 1.0]), synth.TREE_KD, synth.PLANE_EQUAL_DENSITY)
+    assert c[0] == pytest.approx(1.0 / 3.0, abs=0.05)
+    # uniform density (rho = 1, so every mean is exactly 1): all planes tie and the middle draw pair wins
+    c = _root_planes(synth.make_const(1.0), synth.TREE_KD, synth.PLANE_EQUAL_DENSITY)
+    assert abs(c[0]) < 0.06
+
+
+SPLIT_VARIANTS = [(synth.TREE_OCTREE, synth.PLANE_BARYCENTRE, 0), (synth.TREE_KD, synth.PLANE_EQUAL_MASS, 0),
+                  (synth.TREE_KD, synth.PLANE_EQUAL_DENSITY, 0), (synth.TREE_KD, synth.PLANE_EQUAL_MASS, 1)]
+SPLIT_IDS = ["octree-barycentre", "kd-equal-mass", "kd-equal-density", "kd-gradient-equal-mass"]
+
+
+def _variant_tree(kind, plane, axis, model=None, delta_max=2e-3, max_level=5):
+    model = synth.make_disk() if model is None else model
+    return oracle.build_tree(model, _bp(kind=kind, delta_max=delta_max, max_level=max_level, split_plane=plane,
+                                        split_axis=axis))
+
+
+@pytest.mark.parametrize("kind,plane,axis", SPLIT_VARIANTS, ids=SPLIT_IDS)
+def test_split_variant_children_tile_their_parents(kind, plane, axis):
+    t = _variant_tree(kind, plane, axis)
+    assert t.n_leaves > 200
+    nch = 8 if kind == synth.TREE_OCTREE else 2
+    off_lattice = 0
+    for nd in np.nonzero(t.child >= 0)[0]:
+        c0 = t.child[nd]
+        lo, hi = t.lo[nd], t.hi[nd]
+        cut = t.hi[c0]
+        for j in range(nch):
+            clo, chi = t.lo[c0 + j], t.hi[c0 + j]
+            for a in range(3):
+                split = (kind == synth.TREE_OCTREE) or cut[a] != hi[a]
+                if not split:
+                    assert clo[a] == lo[a] and chi[a] == hi[a]
+                    continue
+                assert lo[a] < cut[a] < hi[a]
+                up = ((j >> a) & 1) if kind == synth.TREE_OCTREE else j
+                assert (clo[a], chi[a]) == ((cut[a], hi[a]) if up else (lo[a], cut[a]))
+                off_lattice += cut[a] != 0.5 * (lo[a] + hi[a])
+    assert off_lattice > 0  # the planes really are not the geometric centres
+    # k-d depth limit and per-axis level limit
+    assert t.lvl.max() <= 5 if kind == synth.TREE_OCTREE else t.lvl.sum(axis=1).max() <= 15
+
+
+def _plane_points(t, rng, n):
+    """Points on the tree's own (non-dyadic) leaf walls, edges and corners, with awkward directions."""
+    leaves = rng.integers(0, t.n_leaves, n)
+    lo, hi = t.leaf_lo[leaves], t.leaf_hi[leaves]
+    p = lo + rng.random((n, 3)) * (hi - lo)
+    pick = rng.random((n, 3))
+    p = np.where(pick < 0.3, lo, np.where(pick < 0.6, hi, p))
+    k = rng.choice([-1.0, -0.0, 0.0, 1.0, 0.3, -0.7], size=(n, 3))
+    return p, k
+
+
+@pytest.mark.parametrize("kind,plane,axis", SPLIT_VARIANTS, ids=SPLIT_IDS)
+def test_split_variant_locate_matches_brute_force(kind, plane, axis):
+    t = _variant_tree(kind, plane, axis)
+    rng = np.random.default_rng(21)
+    p = rng.uniform(-1, 1, size=(2000, 3))
+    k = synth.isotropic_dirs(rng, 2000)
+    pl, kl = _plane_points(t, rng, 3000)
+    P, K = np.vstack([p, pl]), np.vstack([k, kl])
+    got = oracle.locate(t, P, K)
+    ref, hits = oracle.brute_locate(t, P, K)
+    inside = hits == 1
+    leaving = np.any(((P == -1.0) & (K < 0)) | ((P == 1.0) & (K > 0)), axis=1)
+    assert (hits <= 1).all()
+    assert (inside == ~leaving).all()
+    np.testing.assert_array_equal(got[inside], ref[inside])
+
+
+@pytest.mark.parametrize("kind,plane,axis", SPLIT_VARIANTS, ids=SPLIT_IDS)
+def test_split_variant_sequences_match_brute_force(kind, plane, axis):
+    t = _variant_tree(kind, plane, axis)
+    o, k = synth.emission_rays(31, 120)
+    r = oracle.trace(t, o, k, emit=True, threads=1)
+    for i in range(o.shape[0]):
+        a, b = r["seg_off"][i], r["seg_off"][i + 1]
+        chord = float(_exact_chord(o[i], k[i]))
+        cells, tin, ds = oracle.brute_sequence(t, o[i], k[i], 0.0, chord * 2)
+        keep = ds > 0
+        np.testing.assert_array_equal(r["seg_cell"][a:b], cells[keep])
+        np.testing.assert_allclose(r["seg_ds"][a:b], ds[keep], rtol=1e-12, atol=1e-15)
+        assert r["seg_ds"][a:b].sum() == pytest.approx(chord, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind,plane", [(synth.TREE_OCTREE, synth.PLANE_BARYCENTRE),
+                                        (synth.TREE_KD, synth.PLANE_EQUAL_MASS),
+                                        (synth.TREE_KD, synth.PLANE_EQUAL_DENSITY)])
+def test_split_variant_uniform_density_tau_closed_form(kind, plane):
+    # uniform rho: the draw-driven planes are not the centres, yet every leaf carries rho0 exactly, so
+    # tau = kappa rho0 chord on every ray
+    rho0, kappa = 2.5, 1.5
+    t = _variant_tree(kind, plane, 0, model=synth.make_const(rho0), delta_max=1.0 / 300, max_level=6)
+    assert t.n_leaves >= 300
+    o, k = synth.emission_rays(6, 300)
+    r = oracle.trace(t, o, k, kappa=kappa)
+    for i in range(300):
+        assert r["tau"][i] == pytest.approx(kappa * rho0 * float(_exact_chord(o[i], k[i])), rel=1e-13)
+
+
+def test_split_location_rejected_for_the_wrong_tree():
+    with pytest.raises(RuntimeError):
+        oracle.build_tree(synth.make_disk(), _bp(kind=synth.TREE_OCTREE, split_plane=synth.PLANE_EQUAL_MASS))
+    with pytest.raises(RuntimeError):
+        oracle.build_tree(synth.make_disk(), _bp(kind=synth.TREE_KD, split_plane=synth.PLANE_BARYCENTRE))
