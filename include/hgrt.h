@@ -101,9 +101,34 @@ typedef struct hg_model {
  * refined beyond the octree-equivalent level and the depth stays at most
  * 3*max_level) the largest positive g_a wins, ties to the lower axis; when
  * none is positive, the first of those axes in cyclic order from the
- * node's depth mod 3.  Either way the split is at the midpoint. */
+ * node's depth mod 3.
+ * Split location (Sect. 2.2), from the node's n_ran draws (positions x_s,
+ * densities r_s, s = 0..n_ran-1):
+ *   HG_PLANE_CENTRE: the geometric centre (the dyadic midpoint);
+ *   HG_PLANE_BARYCENTRE (octrees): the three planes through the centre of
+ *     mass sum(r_s x_s) / sum(r_s), sums in draw order;
+ *   HG_PLANE_EQUAL_MASS (k-d trees): with the draws ordered by their
+ *     coordinate on the split axis (ties by s), the plane between draws j
+ *     and j+1 for the first j whose running density sum C_j (left to right)
+ *     satisfies 2 C_j >= C_total, but at most n_ran-2;
+ *   HG_PLANE_EQUAL_DENSITY (k-d trees): the plane between draws j and j+1
+ *     minimising |C_j/(j+1) - R_j/(n_ran-1-j)| (R_j the sum right of the
+ *     plane, added right to left) over the j whose draws differ in
+ *     position; ties to the smallest |2j - (n_ran-2)|, then the smaller j.
+ * A plane between draws sits at x_j + (x_{j+1} - x_j)/2.  Without mass (or
+ * usable draws), or when that value is not strictly inside the node, the
+ * node's centre lo + (hi - lo)/2 is used; a node too thin to hold any plane
+ * strictly inside stays a leaf.  With a location other than the centre the
+ * gradient orientation compares the draws below and above lo + (hi - lo)/2.
+ * Such trees have FP64 node boxes that are no dyadic lattice cells; their
+ * neighbor lists are found and sorted with FP64 box arithmetic.  The level
+ * and index outputs still count the halvings per axis (they key the draws). */
 #define HG_AXIS_CYCLIC 0
 #define HG_AXIS_GRADIENT 1
+#define HG_PLANE_CENTRE 0
+#define HG_PLANE_BARYCENTRE 1
+#define HG_PLANE_EQUAL_MASS 2
+#define HG_PLANE_EQUAL_DENSITY 3
 typedef struct hg_build_params {
     int32_t kind; /* HG_OCTREE or HG_KDTREE */
     int32_t use_delta, use_tau, use_q;
@@ -112,8 +137,9 @@ typedef struct hg_build_params {
     int32_t n_ran;     /* >= 1 */
     uint64_t seed;
     int64_t max_nodes; /* 0 = unlimited; otherwise the build fails with HG_EOVERFLOW beyond it */
-    int32_t split_axis; /* k-d trees: HG_AXIS_CYCLIC or HG_AXIS_GRADIENT; ignored for octrees */
-    int32_t reserved;   /* 0 */
+    int32_t split_axis;  /* k-d trees: HG_AXIS_CYCLIC or HG_AXIS_GRADIENT; ignored for octrees */
+    int32_t split_plane; /* HG_PLANE_CENTRE; octrees also HG_PLANE_BARYCENTRE; k-d trees also
+                            HG_PLANE_EQUAL_MASS or HG_PLANE_EQUAL_DENSITY (host builder only) */
 } hg_build_params;
 
 /* Flat description of a grid: the node list of Sect. 2.2 (root first,
@@ -190,7 +216,12 @@ typedef struct hg_grid_info {
     int64_t device_bytes;   /* HBM held by the grid */
     int64_t long_walls;     /* walls whose list is longer than the scan limit (searched top-down) */
     double lo[3], hi[3];
+    int32_t nav;            /* HG_NAV_NEIGHBOR_LISTS or HG_NAV_ROPES: how the next leaf is found */
+    int32_t reserved;
 } hg_grid_info;
+
+#define HG_NAV_NEIGHBOR_LISTS 0
+#define HG_NAV_ROPES 1
 
 /* Upload a grid: the node list of Sect. 2.2 and the six per-leaf neighbor
  * lists of Sect. 2.3 (built once with the grid, sorted by decreasing overlap
@@ -205,6 +236,32 @@ typedef struct hg_grid_info {
 hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate, hg_grid **out);
 void hg_free_grid(hg_grid *g);
 hg_status hg_grid_get_info(const hg_grid *g, hg_grid_info *out);
+
+/* Ropes: the alternative to neighbor lists from the ray-shooting literature
+ * that Sect. 1 and 2.3 set the paper's method against (stackless k-d
+ * traversal, one link per leaf wall).  The rope of a leaf wall is the
+ * deepest node lying across the wall (on its far side, touching it) whose
+ * box covers the wall's whole face; it is found by a descent from the root
+ * that continues while exactly one child covers the face.  A path leaving a
+ * leaf through that wall goes to the rope's node and, when that is not a
+ * leaf, locates its exit point top-down below it instead of from the root;
+ * an exit point the rope's leaf does not hold (edge and corner exits) is
+ * located from the root, as with neighbor lists.  Results are those of the
+ * neighbor-list walk: the next leaf is the one the contract defines.
+ * hg_build_ropes writes ropes[6 i + w] for leaf i, wall w (-x,+x,-y,+y,-z,
+ * +z): the leaf id (>= 0), -1 on the domain boundary, or -2 - node for an
+ * internal node.  desc: host arrays (the neighbor lists are not read);
+ * ropes: host int32[6 n_leaves], caller-owned; n_threads <= 0: all cores.
+ * HG_EFORMAT for leaf ids that do not match the node list. */
+hg_status hg_build_ropes(const hg_grid_desc *desc, int32_t n_threads, int32_t *ropes);
+/* hg_load_grid for the rope walk: each leaf record's six wall slots hold
+ * ropes (from hg_build_ropes; NULL: built here with all cores) instead of
+ * the neighbor-list heads, and no list tails are stored (the description's
+ * neighbor lists may be NULL).  Every walk of the library then follows
+ * ropes on this grid.  With validate != 0 the node list is checked as by
+ * hg_load_grid and every rope must lie across its wall and cover its face
+ * (HG_EFORMAT otherwise). */
+hg_status hg_load_grid_ropes(const hg_grid_desc *desc, const int32_t *ropes, int32_t validate, hg_grid **out);
 
 /* ------------------------------------------------------------------------ path calculation
  * A path is x(t) = o + t d for t in [t_start, t_end]: t_start = 0 for an

@@ -55,7 +55,7 @@ class _BuildParams(C.Structure):
                 ("delta_max", C.c_double), ("tau_max", C.c_double), ("q_max", C.c_double),
                 ("kappa", C.c_double), ("max_level", C.c_int32), ("n_ran", C.c_int32),
                 ("seed", C.c_uint64), ("max_nodes", C.c_int64), ("split_axis", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("split_plane", C.c_int32)]
 
 
 class _Desc(C.Structure):
@@ -75,7 +75,11 @@ class _HostNodes(C.Structure):
 class _GridInfo(C.Structure):
     _fields_ = [("kind", C.c_int32), ("max_depth", C.c_int32), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
                 ("n_tail", C.c_int64), ("device_bytes", C.c_int64), ("long_walls", C.c_int64),
-                ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("nav", C.c_int32), ("reserved", C.c_int32)]
+
+
+NAV_NEIGHBOR_LISTS = 0  # HG_NAV_NEIGHBOR_LISTS
+NAV_ROPES = 1           # HG_NAV_ROPES
 
 
 class TraceOpts(C.Structure):
@@ -102,6 +106,8 @@ _SIGS = {
     "hg_host_grid_nodes": (_S, [_V, C.POINTER(_HostNodes)]),
     "hg_free_host_grid": (None, [_V]),
     "hg_load_grid": (_S, [C.POINTER(_Desc), C.c_int32, C.POINTER(_V)]),
+    "hg_build_ropes": (_S, [C.POINTER(_Desc), C.c_int32, C.POINTER(C.c_int32)]),
+    "hg_load_grid_ropes": (_S, [C.POINTER(_Desc), C.POINTER(C.c_int32), C.c_int32, C.POINTER(_V)]),
     "hg_free_grid": (None, [_V]),
     "hg_grid_get_info": (_S, [_V, C.POINTER(_GridInfo)]),
     "hg_trace_rays": (_S, [_V, _I64, _V, _V, _V, C.c_double, C.POINTER(TraceOpts), _V, _V, _V, _V]),
@@ -285,6 +291,7 @@ def _build_params(params):
     p.seed = int(params.seed) & ((1 << 64) - 1)
     p.max_nodes = int(getattr(params, "max_nodes", 0) or 0)
     p.split_axis = int(getattr(params, "split_axis", 0) or 0)
+    p.split_plane = int(getattr(params, "split_plane", 0) or 0)
     return p
 
 
@@ -369,6 +376,7 @@ class Grid:
         self.long_walls = int(info.long_walls)
         self.lo = tuple(info.lo)
         self.hi = tuple(info.hi)
+        self.nav = int(info.nav)
 
     @property
     def handle(self):
@@ -386,14 +394,38 @@ class Grid:
             pass
 
 
-def load_grid(desc, validate: bool = True) -> Grid:
-    """Upload a grid (a HostGrid or GridDesc) to the current CUDA device."""
+def load_grid(desc, validate: bool = True, nav: str = "lists", ropes=None) -> Grid:
+    """Upload a grid (a HostGrid or GridDesc) to the current CUDA device.  nav="lists": the next leaf
+    from the neighbor lists (hg_load_grid); nav="ropes": from ropes (hg_load_grid_ropes), given as an
+    int32 [n_leaves, 6] array or built by the library when None."""
     if isinstance(desc, HostGrid):
         desc = desc.desc()
     d, _keep = desc.struct()
     h = C.c_void_p()
-    _check(_lib.hg_load_grid(C.byref(d), int(bool(validate)), C.byref(h)), "hg_load_grid")
+    if nav == "lists":
+        _check(_lib.hg_load_grid(C.byref(d), int(bool(validate)), C.byref(h)), "hg_load_grid")
+    elif nav == "ropes":
+        rp = None
+        if ropes is not None:
+            ropes = np.ascontiguousarray(ropes, np.int32)
+            if ropes.size != 6 * d.n_leaves:
+                raise ValueError("ropes needs 6 entries per leaf")
+            rp = _np_ptr(ropes, C.c_int32)
+        _check(_lib.hg_load_grid_ropes(C.byref(d), rp, int(bool(validate)), C.byref(h)), "hg_load_grid_ropes")
+    else:
+        raise ValueError("nav must be 'lists' or 'ropes'")
     return Grid(h)
+
+
+def build_ropes(desc, threads: int = 0) -> np.ndarray:
+    """hg_build_ropes: per leaf and wall (-x,+x,-y,+y,-z,+z) the leaf id, -1 on the domain boundary, or
+    -2 - node for an internal node; int32 [n_leaves, 6]."""
+    if isinstance(desc, HostGrid):
+        desc = desc.desc()
+    d, _keep = desc.struct()
+    out = np.empty((d.n_leaves, 6), np.int32)
+    _check(_lib.hg_build_ropes(C.byref(d), int(threads), _np_ptr(out, C.c_int32)), "hg_build_ropes")
+    return out
 
 
 # ----------------------------------------------------------------------------- path calculation

@@ -100,7 +100,8 @@ struct BatchRays {
     }
 };
 
-template <int PREC>
+// NAV: 0 every grid holds neighbor lists, 1 every grid ropes, 2 a mix (read per grid).
+template <int PREC, int NAV>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
     __shared__ int64_t s_qbeg[kMaxBatch + 1];
     __shared__ int32_t s_perm[kMaxBatch];
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
     io.tau = A.tau;
     io.ncross = A.ncross;
     io.status = A.status;
-    walk_loop<2, MODE_TAU, PREC>(src, io, nullptr, 0);
+    walk_loop<2, MODE_TAU, PREC, NAV>(src, io, nullptr, 0);
 }
 
 }  // namespace hg
@@ -130,6 +131,7 @@ struct hg_batch {
     int32_t *d_perm = nullptr;
     unsigned long long *d_counter = nullptr;
     int device = 0;
+    int nav = 0;  // 0 all grids with neighbor lists, 1 all with ropes, 2 mixed
 };
 
 using namespace hg;
@@ -167,6 +169,9 @@ extern "C" hg_status hg_batch_create(int32_t n_grids, const hg_grid *const *grid
     for (int s = 0; s < n_grids; s++) qbeg[s + 1] = qbeg[s] + cnt[perm[s]];
     hg_batch *b = new hg_batch();
     b->n_grids = n_grids;
+    int n_ropes = 0;
+    for (int i = 0; i < n_grids; i++) n_ropes += grids[i]->d.nav == HG_NAV_ROPES ? 1 : 0;
+    b->nav = n_ropes == 0 ? 0 : (n_ropes == n_grids ? 1 : 2);
     b->total = qbeg[n_grids];
     cudaGetDevice(&b->device);
     cudaError_t e = cudaMalloc(&b->d_entries, ent.size() * sizeof(BatchEntry));
@@ -227,7 +232,11 @@ extern "C" hg_status hg_batch_trace(hg_batch *b, const double *o, const double *
         set_error("hg_batch_trace: block must be a multiple of 32 in 32..256");
         return HG_EINVAL;
     }
-    auto kern = (prec == HG_FP64) ? &batch_kernel<HG_FP64> : &batch_kernel<HG_FP32K>;
+    using BatchFn = void (*)(const BatchArgs);
+    static const BatchFn kernels[2][3] = {{&batch_kernel<HG_FP64, 0>, &batch_kernel<HG_FP64, 1>, &batch_kernel<HG_FP64, 2>},
+                                          {&batch_kernel<HG_FP32K, 0>, &batch_kernel<HG_FP32K, 1>,
+                                           &batch_kernel<HG_FP32K, 2>}};
+    const BatchFn kern = kernels[prec == HG_FP64 ? 0 : 1][b->nav];
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
     if (e != cudaSuccess) return cuda_err(e, "batch occupancy");

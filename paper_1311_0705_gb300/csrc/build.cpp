@@ -117,6 +117,89 @@ struct HostModel {
 
 };
 
+// Split planes at a location other than the centre (Sect. 2.2), from a
+// node's n draws (see hg_build_params in hgrt.h for the definitions).
+double box_centre(double lo, double hi) { return lo + 0.5 * (hi - lo); }
+
+// Octree: the three planes through the draws' centre of mass.
+void barycentre_planes(const hg::Draw *d, int32_t n, const double *lo, const double *hi, double *c) {
+    double S = 0.0, Sx[3] = {0.0, 0.0, 0.0};
+    for (int32_t s = 0; s < n; s++) {
+        S += d[s].r;
+        for (int a = 0; a < 3; a++) Sx[a] += d[s].r * d[s].x[a];
+    }
+    for (int a = 0; a < 3; a++) {
+        double v = (S > 0.0) ? Sx[a] / S : box_centre(lo[a], hi[a]);
+        c[a] = (lo[a] < v && v < hi[a]) ? v : box_centre(lo[a], hi[a]);
+    }
+}
+
+// k-d tree: the equal-mass or equal-mean-density plane on axis a.  Reorders d.
+double kd_plane(int mode, hg::Draw *d, int32_t n, int a, double lo, double hi, std::vector<double> &right) {
+    const double centre = box_centre(lo, hi);
+    if (n < 2) return centre;
+    std::sort(d, d + n, [a](const hg::Draw &p, const hg::Draw &q) {
+        return p.x[a] < q.x[a] || (p.x[a] == q.x[a] && p.s < q.s);
+    });
+    int32_t j = -1;
+    if (mode == HG_PLANE_EQUAL_MASS) {
+        double total = 0.0;
+        for (int32_t k = 0; k < n; k++) total += d[k].r;
+        if (!(total > 0.0)) return centre;
+        double run = 0.0;
+        for (int32_t k = 0; k < n; k++) {
+            run += d[k].r;
+            if (2.0 * run >= total) {
+                j = k;
+                break;
+            }
+        }
+        if (j == n - 1) j = n - 2;
+        if (j < 0 || !(d[j].x[a] < d[j + 1].x[a])) return centre;
+    } else {
+        // right[k]: the density sum of draws k+1 .. n-1, added right to left
+        right.assign((size_t)n, 0.0);
+        double r = 0.0;
+        for (int32_t k = n - 1; k >= 1; k--) {
+            r += d[k].r;
+            right[(size_t)k - 1] = r;
+        }
+        double left = 0.0, best = 0.0;
+        int32_t best_mid = 0;
+        for (int32_t k = 0; k <= n - 2; k++) {
+            left += d[k].r;
+            if (!(d[k].x[a] < d[k + 1].x[a])) continue;
+            const double diff = std::fabs(left / (double)(k + 1) - right[(size_t)k] / (double)(n - 1 - k));
+            const int32_t mid = std::abs(2 * k - (n - 2));
+            if (j < 0 || diff < best || (diff == best && mid < best_mid)) {
+                j = k;
+                best = diff;
+                best_mid = mid;
+            }
+        }
+        if (j < 0) return centre;
+    }
+    const double v = d[j].x[a] + 0.5 * (d[j + 1].x[a] - d[j].x[a]);
+    return (lo < v && v < hi) ? v : centre;
+}
+
+// Where a node that the criteria subdivide is cut (planes[3]); clears
+// st.sub when the box has no room for a plane strictly inside on a cut axis.
+void place_planes(const hg_build_params &P, const double *lo, const double *hi, hg::Draw *d,
+                  std::vector<double> &scratch, hg::NodeStats &st, double *planes) {
+    for (int a = 0; a < 3; a++) planes[a] = box_centre(lo[a], hi[a]);
+    if (st.sub) {
+        if (P.kind == HG_OCTREE)
+            barycentre_planes(d, P.n_ran, lo, hi, planes);
+        else
+            planes[st.axis] = kd_plane(P.split_plane, d, P.n_ran, st.axis, lo[st.axis], hi[st.axis], scratch);
+    }
+    for (int a = 0; a < 3; a++) {
+        if (P.kind == HG_KDTREE && a != st.axis) continue;
+        if (!(lo[a] < planes[a] && planes[a] < hi[a])) st.sub = 0;
+    }
+}
+
 }  // namespace
 
 struct hg_host_grid {
@@ -134,6 +217,72 @@ struct hg_host_grid {
 };
 
 namespace {
+
+// Neighbor lists from the FP64 boxes, for trees whose planes are not dyadic:
+// the same descent as below, with exact comparisons of the stored bounds;
+// overlap areas (the sort key) are products of FP64 differences.
+void build_neighbors_fp64(hg_host_grid &G, int threads) {
+    const int64_t nl = (int64_t)G.leaf_node.size();
+    const double *dlo = &G.lo[0], *dhi = &G.hi[0];  // the root's box
+    const int nch = (G.kind == HG_OCTREE) ? 8 : 2;
+    auto walk = [&](int64_t ln, int w, std::vector<int64_t> &stack, auto &&fn) {
+        const int a = w >> 1, s = w & 1;
+        const double *L = &G.lo[3 * ln], *H = &G.hi[3 * ln];
+        const double P = s ? H[a] : L[a];
+        if ((s && P == dhi[a]) || (!s && P == dlo[a])) return;
+        stack.clear();
+        stack.push_back(0);
+        while (!stack.empty()) {
+            const int64_t nd = stack.back();
+            stack.pop_back();
+            const double *nlo = &G.lo[3 * nd], *nhi = &G.hi[3 * nd];
+            const bool across = s ? (nlo[a] <= P && P < nhi[a]) : (nlo[a] < P && P <= nhi[a]);
+            if (!across) continue;
+            double area = 1.0;
+            bool ok = true;
+            for (int b = 0; b < 3; b++) {
+                if (b == a) continue;
+                const double hi_b = std::min(nhi[b], H[b]), lo_b = std::max(nlo[b], L[b]);
+                if (!(hi_b > lo_b)) {
+                    ok = false;
+                    break;
+                }
+                area *= hi_b - lo_b;
+            }
+            if (!ok) continue;
+            if (G.child[nd] < 0) {
+                fn(G.leaf[nd], area);
+            } else {
+                for (int c = nch - 1; c >= 0; c--) stack.push_back(G.child[nd] + c);
+            }
+        }
+    };
+    std::vector<int64_t> counts((size_t)nl * 6, 0);
+    parallel_for(nl, threads, [&](int64_t a0, int64_t a1) {
+        std::vector<int64_t> stack;
+        for (int64_t i = a0; i < a1; i++)
+            for (int w = 0; w < 6; w++) {
+                int64_t c = 0;
+                walk(G.leaf_node[i], w, stack, [&](int32_t, double) { c++; });
+                counts[6 * i + w] = c;
+            }
+    });
+    G.nbr_off.assign((size_t)nl * 6 + 1, 0);
+    for (int64_t j = 0; j < nl * 6; j++) G.nbr_off[j + 1] = G.nbr_off[j] + counts[j];
+    G.nbr_id.assign((size_t)G.nbr_off[nl * 6], 0);
+    parallel_for(nl, threads, [&](int64_t a0, int64_t a1) {
+        std::vector<int64_t> stack;
+        std::vector<std::pair<double, int32_t>> buf;
+        for (int64_t i = a0; i < a1; i++)
+            for (int w = 0; w < 6; w++) {
+                buf.clear();
+                walk(G.leaf_node[i], w, stack, [&](int32_t id, double area) { buf.emplace_back(-area, id); });
+                std::sort(buf.begin(), buf.end());
+                const int64_t o = G.nbr_off[6 * i + w];
+                for (size_t e = 0; e < buf.size(); e++) G.nbr_id[o + e] = buf[e].second;
+            }
+    });
+}
 
 // Neighbor lists in lattice units of the finest per-axis level.
 void build_neighbors(hg_host_grid &G, int threads) {
@@ -227,6 +376,14 @@ hg_status check_build_args(const char *name, const hg_model *model, const hg_bui
         hg::set_error("%s: split_axis must be HG_AXIS_CYCLIC or HG_AXIS_GRADIENT", name);
         return HG_EINVAL;
     }
+    const bool plane_ok = P.split_plane == HG_PLANE_CENTRE ||
+                          (P.kind == HG_OCTREE && P.split_plane == HG_PLANE_BARYCENTRE) ||
+                          (P.kind == HG_KDTREE &&
+                           (P.split_plane == HG_PLANE_EQUAL_MASS || P.split_plane == HG_PLANE_EQUAL_DENSITY));
+    if (!plane_ok) {
+        hg::set_error("%s: split_plane %d is not a location for this kind of tree", name, P.split_plane);
+        return HG_EINVAL;
+    }
     if (!(model->m_tot > 0.0)) { hg::set_error("%s: m_tot must be > 0", name); return HG_EINVAL; }
     if (model->kind < HG_MODEL_CONST || model->kind > HG_MODEL_DYADIC) {
         hg::set_error("%s: bad model kind %d", name, model->kind);
@@ -245,29 +402,34 @@ hg_status check_build_args(const char *name, const hg_model *model, const hg_bui
 // [begin, end) (their levels and indices are in G), then the nodes to
 // subdivide get their children appended in parent order.  Leaves are
 // numbered in node order (the caller builds the neighbor lists).
+// With split planes other than the centre, eval also fills planes (3 per
+// node of the level) and each child's box is cut from its parent's there.
 template <class Eval>
 hg_status build_levels(const HostModel &M, const hg_build_params &P, hg_host_grid &G, Eval &&eval) {
     const hg::ModelView V = M.view();
-    auto push = [&](const int32_t *l, const int64_t *i) {
+    auto push = [&](const int32_t *l, const int64_t *i, const double *lo, const double *hi) {
         for (int a = 0; a < 3; a++) {
             G.lvl.push_back(l[a]);
             G.idx.push_back(i[a]);
-            G.lo.push_back(hg::model_bound(V, a, i[a], l[a]));
-            G.hi.push_back(hg::model_bound(V, a, i[a] + 1, l[a]));
+            G.lo.push_back(lo ? lo[a] : hg::model_bound(V, a, i[a], l[a]));
+            G.hi.push_back(hi ? hi[a] : hg::model_bound(V, a, i[a] + 1, l[a]));
         }
         G.child.push_back(-1);
         G.leaf.push_back(-1);
     };
+    const bool centre = (P.split_plane == HG_PLANE_CENTRE);
+    std::vector<double> planes;
     G.kind = P.kind;
     int32_t l0[3] = {0, 0, 0};
     int64_t i0[3] = {0, 0, 0};
-    push(l0, i0);
+    push(l0, i0, nullptr, nullptr);
     int64_t begin = 0;
     std::vector<hg::NodeStats> st;
     while (begin < (int64_t)G.child.size()) {
         const int64_t end = (int64_t)G.child.size();
         st.assign((size_t)(end - begin), hg::NodeStats{});
-        hg_status hs = eval(begin, end, st);
+        if (!centre) planes.assign((size_t)(end - begin) * 3, 0.0);
+        hg_status hs = eval(begin, end, st, planes);
         if (hs != HG_OK) return hs;
         for (int64_t j = 0; j < end - begin; j++) {
             G.rho.push_back(st[j].rho);
@@ -291,19 +453,23 @@ hg_status build_levels(const HostModel &M, const hg_build_params &P, hg_host_gri
             int32_t l[3] = {G.lvl[3 * nd], G.lvl[3 * nd + 1], G.lvl[3 * nd + 2]};
             int64_t i[3] = {G.idx[3 * nd], G.idx[3 * nd + 1], G.idx[3 * nd + 2]};
             const int axis = st[nd - begin].axis;  // k-d: the split axis (octree: -1)
+            const double plo[3] = {G.lo[3 * nd], G.lo[3 * nd + 1], G.lo[3 * nd + 2]};
+            const double phi[3] = {G.hi[3 * nd], G.hi[3 * nd + 1], G.hi[3 * nd + 2]};
             for (int c = 0; c < nch; c++) {
                 int32_t lc[3] = {l[0], l[1], l[2]};
                 int64_t ic[3] = {i[0], i[1], i[2]};
-                if (axis < 0) {
-                    for (int a = 0; a < 3; a++) {
-                        lc[a] = l[a] + 1;
-                        ic[a] = 2 * i[a] + ((c >> a) & 1);
-                    }
-                } else {
-                    lc[axis] = l[axis] + 1;
-                    ic[axis] = 2 * i[axis] + c;
+                double clo[3] = {plo[0], plo[1], plo[2]}, chi[3] = {phi[0], phi[1], phi[2]};
+                for (int a = 0; a < 3; a++) {
+                    if (axis >= 0 && a != axis) continue;
+                    const int up = (axis < 0) ? ((c >> a) & 1) : c;
+                    lc[a] = l[a] + 1;
+                    ic[a] = 2 * i[a] + up;
+                    if (!centre) (up ? clo[a] : chi[a]) = planes[3 * (size_t)(nd - begin) + a];
                 }
-                push(lc, ic);
+                if (centre)
+                    push(lc, ic, nullptr, nullptr);
+                else
+                    push(lc, ic, clo, chi);
             }
         }
         begin = end;
@@ -336,19 +502,34 @@ extern "C" hg_status hg_build_grid(const hg_model *model, const hg_build_params 
     try {
         M.init(*model);
         const hg::ModelView V = M.view();
-        hs = build_levels(M, P, *G, [&](int64_t begin, int64_t end, std::vector<hg::NodeStats> &st) {
+        const bool centre = (P.split_plane == HG_PLANE_CENTRE);
+        hs = build_levels(M, P, *G, [&](int64_t begin, int64_t end, std::vector<hg::NodeStats> &st,
+                                        std::vector<double> &planes) {
             parallel_for(end - begin, threads, [&](int64_t a0, int64_t a1) {
+                std::vector<hg::Draw> draws(centre ? 0 : (size_t)P.n_ran);
+                std::vector<double> scratch;
                 for (int64_t j = a0; j < a1; j++) {
                     const int64_t nd = begin + j;
                     const int32_t *l = &G->lvl[3 * nd];
                     const int64_t *i = &G->idx[3 * nd];
                     const int32_t depth = (P.kind == HG_OCTREE) ? l[0] : l[0] + l[1] + l[2];
-                    st[j] = hg::eval_node_stats(V, P, l, i, depth);
+                    if (centre) {
+                        st[j] = hg::eval_node_stats(V, P, l, i, depth);
+                    } else {
+                        const double *lo = &G->lo[3 * nd], *hi = &G->hi[3 * nd];
+                        st[j] = hg::eval_node_stats(V, P, l, i, depth, lo, hi, draws.data());
+                        place_planes(P, lo, hi, draws.data(), scratch, st[j], &planes[3 * (size_t)j]);
+                    }
                 }
             });
             return HG_OK;
         });
-        if (hs == HG_OK) build_neighbors(*G, threads);
+        if (hs == HG_OK) {
+            if (centre)
+                build_neighbors(*G, threads);
+            else
+                build_neighbors_fp64(*G, threads);
+        }
     } catch (const std::bad_alloc &) {
         hg::set_error("hg_build_grid: out of host memory");
         return HG_ENOMEM;
@@ -362,6 +543,10 @@ extern "C" hg_status hg_build_grid_gpu(const hg_model *model, const hg_build_par
                                        hg_host_grid **out) {
     hg_status hs = check_build_args("hg_build_grid_gpu", model, params, out);
     if (hs != HG_OK) return hs;
+    if (params->split_plane != HG_PLANE_CENTRE) {
+        hg::set_error("hg_build_grid_gpu: split planes other than the centre are built by hg_build_grid only");
+        return HG_EINVAL;
+    }
     *out = nullptr;
     const hg_build_params P = *params;
     std::unique_ptr<hg_host_grid> G(new hg_host_grid());

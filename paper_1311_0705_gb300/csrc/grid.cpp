@@ -4,7 +4,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
+#include <system_error>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "hg_internal.h"
@@ -18,7 +21,7 @@ hg_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? HG_ENOMEM : HG_ECUDA;
 }
 
-hg_status validate(const hg_grid_desc &D) {
+hg_status validate(const hg_grid_desc &D, bool check_lists) {
     const int64_t n = D.n_nodes, nl = D.n_leaves;
     const int nch = (D.kind == HG_OCTREE) ? 8 : 2;
     std::vector<int32_t> parent((size_t)n, -1);
@@ -111,6 +114,7 @@ hg_status validate(const hg_grid_desc &D) {
             hg::set_error("leaf %lld has a non-finite density", (long long)j);
             return HG_EFORMAT;
         }
+    if (!check_lists) return HG_OK;
     // neighbor lists: adjacency, positive overlap, tiling, order
     if (D.nbr_off[0] != 0) { hg::set_error("nbr_off[0] must be 0"); return HG_EFORMAT; }
     const double *dlo = D.node_lo, *dhi = D.node_hi;
@@ -160,15 +164,159 @@ hg_status validate(const hg_grid_desc &D) {
     return HG_OK;
 }
 
+// Does node nd lie across leaf wall (a, s) at plane P -- on the far side of
+// it, touching it -- and cover the wall's face [flo, fhi] on the two other
+// axes?
+bool rope_covers(const hg_grid_desc &D, int64_t nd, int a, int s, double P, const double *flo, const double *fhi) {
+    const double *lo = D.node_lo + 3 * nd, *hi = D.node_hi + 3 * nd;
+    const bool across = s ? (lo[a] <= P && P < hi[a]) : (lo[a] < P && P <= hi[a]);
+    if (!across) return false;
+    for (int b = 0; b < 3; b++)
+        if (b != a && !(lo[b] <= flo[b] && fhi[b] <= hi[b])) return false;
+    return true;
+}
+
+// The rope of wall w of the leaf node ln: the deepest node across the wall
+// that covers the whole face, found by a descent from the root that goes on
+// while exactly one child covers it.  Encoded as the leaf id (>= 0), -1 on
+// the domain boundary, or -2 - node for an internal node.
+int32_t rope_of(const hg_grid_desc &D, int64_t ln, int w) {
+    const int a = w >> 1, s = w & 1;
+    const double *flo = D.node_lo + 3 * ln, *fhi = D.node_hi + 3 * ln;
+    const double P = s ? fhi[a] : flo[a];
+    if (P == (s ? D.node_hi[a] : D.node_lo[a])) return -1;
+    const int nch = (D.kind == HG_OCTREE) ? 8 : 2;
+    int64_t nd = 0;
+    for (;;) {
+        const int32_t c = D.child_first[nd];
+        if (c < 0) return D.node_leaf[nd];
+        int64_t next = -1;
+        int hits = 0;
+        for (int j = 0; j < nch; j++)
+            if (rope_covers(D, (int64_t)c + j, a, s, P, flo, fhi)) {
+                next = (int64_t)c + j;
+                hits++;
+            }
+        if (hits != 1) return (int32_t)(-2 - nd);
+        nd = next;
+    }
+}
+
+// Every rope target must lie across its wall and cover the face (then a
+// descent from it reaches the leaf holding any exit point of the face);
+// exactly the walls on the domain boundary have none.
+hg_status validate_ropes(const hg_grid_desc &D, const std::vector<int64_t> &leaf_node, const int32_t *ropes) {
+    const int64_t nl = D.n_leaves, n = D.n_nodes;
+    for (int64_t i = 0; i < nl; i++) {
+        const int64_t ln = leaf_node[(size_t)i];
+        const double *flo = D.node_lo + 3 * ln, *fhi = D.node_hi + 3 * ln;
+        for (int w = 0; w < 6; w++) {
+            const int a = w >> 1, s = w & 1;
+            const double P = s ? fhi[a] : flo[a];
+            const bool boundary = P == (s ? D.node_hi[a] : D.node_lo[a]);
+            const int32_t r = ropes[6 * i + w];
+            int64_t nd = -1;
+            if (r >= 0 && r < nl) nd = leaf_node[(size_t)r];
+            if (r <= -2 && -2 - (int64_t)r < n) nd = -2 - (int64_t)r;
+            if (boundary ? (r != -1) : (nd < 0 || !rope_covers(D, nd, a, s, P, flo, fhi))) {
+                hg::set_error("leaf %lld wall %d: rope %d does not cover the wall", (long long)i, w, r);
+                return HG_EFORMAT;
+            }
+        }
+    }
+    return HG_OK;
+}
+
+hg_status load_grid_impl(const hg_grid_desc *desc, const int32_t *ropes, int32_t validate_flag, hg_grid **out);
+
 }  // namespace
 
+extern "C" hg_status hg_build_ropes(const hg_grid_desc *desc, int32_t n_threads, int32_t *ropes) {
+    if (!desc || !ropes || desc->n_leaves < 1 || desc->n_nodes < 1 || !desc->node_lo || !desc->node_hi ||
+        !desc->child_first || !desc->node_leaf || (desc->kind != HG_OCTREE && desc->kind != HG_KDTREE)) {
+        hg::set_error("hg_build_ropes: incomplete description or no output");
+        return HG_EINVAL;
+    }
+    const hg_grid_desc D = *desc;
+    try {
+        std::vector<int64_t> leaf_node((size_t)D.n_leaves, -1);
+        const int nch = (D.kind == HG_OCTREE) ? 8 : 2;
+        for (int64_t i = 0; i < D.n_nodes; i++) {
+            const int32_t l = D.node_leaf[i], c = D.child_first[i];
+            if (l >= D.n_leaves || (l >= 0) == (c >= 0) || (c >= 0 && (c <= i || (int64_t)c + nch > D.n_nodes))) {
+                hg::set_error("hg_build_ropes: bad leaf id or child link at node %lld", (long long)i);
+                return HG_EFORMAT;
+            }
+            if (l >= 0) leaf_node[(size_t)l] = i;
+        }
+        for (int64_t i = 0; i < D.n_leaves; i++)
+            if (leaf_node[(size_t)i] < 0) {
+                hg::set_error("hg_build_ropes: leaf %lld has no node", (long long)i);
+                return HG_EFORMAT;
+            }
+        const int threads = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+        std::atomic<int64_t> next{0};
+        const int64_t chunk = 4096;
+        auto work = [&]() {
+            for (;;) {
+                const int64_t a0 = next.fetch_add(chunk);
+                if (a0 >= D.n_leaves) break;
+                const int64_t a1 = std::min(D.n_leaves, a0 + chunk);
+                for (int64_t i = a0; i < a1; i++)
+                    for (int w = 0; w < 6; w++) ropes[6 * i + w] = rope_of(D, leaf_node[(size_t)i], w);
+            }
+        };
+        if (threads <= 1 || D.n_leaves < 2 * chunk) {
+            work();
+        } else {
+            std::vector<std::thread> pool;
+            for (int t = 0; t < threads; t++) pool.emplace_back(work);
+            for (auto &th : pool) th.join();
+        }
+    } catch (const std::bad_alloc &) {
+        hg::set_error("hg_build_ropes: out of host memory");
+        return HG_ENOMEM;
+    } catch (const std::system_error &) {
+        hg::set_error("hg_build_ropes: could not start threads");
+        return HG_EINVAL;
+    }
+    return HG_OK;
+}
+
 extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_flag, hg_grid **out) {
+    return load_grid_impl(desc, nullptr, validate_flag, out);
+}
+
+extern "C" hg_status hg_load_grid_ropes(const hg_grid_desc *desc, const int32_t *ropes, int32_t validate_flag,
+                                        hg_grid **out) {
+    if (!desc || !out) { hg::set_error("hg_load_grid_ropes: null argument"); return HG_EINVAL; }
+    std::vector<int32_t> own;
+    if (!ropes) {
+        try {
+            own.resize((size_t)std::max<int64_t>(desc->n_leaves, 1) * 6);
+        } catch (const std::bad_alloc &) {
+            hg::set_error("hg_load_grid_ropes: out of host memory");
+            return HG_ENOMEM;
+        }
+        hg_status st = hg_build_ropes(desc, 0, own.data());
+        if (st != HG_OK) return st;
+        ropes = own.data();
+    }
+    return load_grid_impl(desc, ropes, validate_flag, out);
+}
+
+namespace {
+
+// Upload a grid; with ropes (host [6 n_leaves]) each leaf record's wall
+// slots hold the ropes instead of the neighbor-list heads, and no list
+// tails are stored.
+hg_status load_grid_impl(const hg_grid_desc *desc, const int32_t *ropes, int32_t validate_flag, hg_grid **out) {
     if (!desc || !out) { hg::set_error("hg_load_grid: null argument"); return HG_EINVAL; }
     *out = nullptr;
     const hg_grid_desc D = *desc;
     if ((D.kind != HG_OCTREE && D.kind != HG_KDTREE) || D.n_nodes < 1 || D.n_leaves < 1 || !D.node_lo ||
-        !D.node_hi || !D.child_first || !D.node_leaf || !D.leaf_rho || !D.nbr_off ||
-        (!D.nbr_id && D.nbr_off[6 * D.n_leaves] > 0)) {
+        !D.node_hi || !D.child_first || !D.node_leaf || !D.leaf_rho ||
+        (!ropes && (!D.nbr_off || (!D.nbr_id && D.nbr_off[6 * D.n_leaves] > 0)))) {
         hg::set_error("hg_load_grid: incomplete description");
         return HG_EINVAL;
     }
@@ -177,8 +325,14 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
         return HG_EINVAL;
     }
     if (validate_flag) {
-        hg_status st = validate(D);
+        hg_status st = validate(D, !ropes);
         if (st != HG_OK) return st;
+        if (ropes) {
+            std::vector<int64_t> ln((size_t)D.n_leaves);
+            for (int64_t i = 0; i < D.n_nodes; i++)
+                if (D.node_leaf[i] >= 0) ln[(size_t)D.node_leaf[i]] = i;
+            if ((st = validate_ropes(D, ln, ropes)) != HG_OK) return st;
+        }
     }
     const int64_t n = D.n_nodes, nl = D.n_leaves;
     std::unique_ptr<hg_grid> g(new hg_grid());
@@ -245,6 +399,13 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
                 return HG_EOVERFLOW;
             }
             R.nbr_base = (uint32_t)tail.size();
+            if (ropes) {
+                for (int w = 0; w < 6; w++) {
+                    R.first[w] = ropes[6 * i + w];
+                    R.cnt[w] = 0;
+                }
+                continue;
+            }
             for (int w = 0; w < 6; w++) {
                 const int64_t b0 = D.nbr_off[6 * i + w], b1 = D.nbr_off[6 * i + w + 1];
                 const int64_t cnt = b1 - b0;
@@ -327,6 +488,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
         G.kind = D.kind;
         G.max_depth = max_depth;
         G.scan_limit = kScanLimit;
+        G.nav = ropes ? HG_NAV_ROPES : HG_NAV_NEIGHBOR_LISTS;
+        G.pad = 0;
         hg_grid_info &I = g->info;
         I.kind = D.kind;
         I.max_depth = max_depth;
@@ -336,6 +499,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
         I.device_bytes = (int64_t)(rec.size() * sizeof(hg::LeafRec) + tail.size() * 4 + nodes.size() +
                                    work.size() * sizeof(float));
         I.long_walls = long_walls;
+        I.nav = ropes ? HG_NAV_ROPES : HG_NAV_NEIGHBOR_LISTS;
+        I.reserved = 0;
         for (int a = 0; a < 3; a++) {
             I.lo[a] = G.dlo[a];
             I.hi[a] = G.dhi[a];
@@ -347,6 +512,8 @@ extern "C" hg_status hg_load_grid(const hg_grid_desc *desc, int32_t validate_fla
     *out = g.release();
     return HG_OK;
 }
+
+}  // namespace
 
 extern "C" void hg_free_grid(hg_grid *g) {
     if (!g) return;

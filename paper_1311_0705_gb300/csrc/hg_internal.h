@@ -79,6 +79,8 @@ struct DevGrid {
     int32_t max_depth;
     int32_t scan_limit;
     int32_t work_n;
+    int32_t nav;  // HG_NAV_NEIGHBOR_LISTS or HG_NAV_ROPES: what the records' wall slots hold
+    int32_t pad;
 };
 
 // Coarse lattice of the expected number of leaf crossings per unit path

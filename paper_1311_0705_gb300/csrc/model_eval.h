@@ -116,6 +116,14 @@ struct NodeStats {
     int32_t axis;  // k-d trees: the axis a subdivision splits (octrees: -1)
 };
 
+// One Monte Carlo draw of a node (position, density, draw number), kept by
+// the host builder to place non-centre split planes.
+struct Draw {
+    double x[3];
+    double r;
+    int32_t s;
+};
+
 // The node with levels l and indices i (depth: its depth in the tree):
 // n_ran draws of its box give rho = mean density, M = V rho, delta = M /
 // M_tot (Eq. 1), tau = kappa M sqrt(a^2 + b^2 + c^2) / (abc) (Eq. 2) and
@@ -127,25 +135,39 @@ struct NodeStats {
 // draws below / at or above the node's midpoint on axis a (ties to the lower
 // axis), among the axes halved fewer than max_level times; when none has a
 // positive g_a, the first of those in cyclic order.
+//
+// box_lo / box_hi: the node's box when it is not the dyadic lattice cell of
+// (l, i) (trees with non-centre split planes), else NULL.  draws: NULL, or
+// room for n_ran draws, which are then recorded.
 HG_HD NodeStats eval_node_stats(const ModelView &M, const hg_build_params &P, const int32_t *l, const int64_t *i,
-                                int32_t depth) {
+                                int32_t depth, const double *box_lo = nullptr, const double *box_hi = nullptr,
+                                Draw *draws = nullptr) {
     double lo[3], hi[3];
     for (int a = 0; a < 3; a++) {
-        lo[a] = model_bound(M, a, i[a], l[a]);
-        hi[a] = model_bound(M, a, i[a] + 1, l[a]);
+        lo[a] = box_lo ? box_lo[a] : model_bound(M, a, i[a], l[a]);
+        hi[a] = box_hi ? box_hi[a] : model_bound(M, a, i[a] + 1, l[a]);
     }
     const uint64_t key = box_key(P.seed, l, i);
     const bool grad = (P.kind == HG_KDTREE && P.split_axis == HG_AXIS_GRADIENT);
     double mid[3] = {0.0, 0.0, 0.0}, s_lo[3] = {0.0, 0.0, 0.0}, s_hi[3] = {0.0, 0.0, 0.0};
     int32_t n_lo[3] = {0, 0, 0};
     if (grad)
-        for (int a = 0; a < 3; a++) mid[a] = model_bound(M, a, 2 * i[a] + 1, l[a] + 1);
+        for (int a = 0; a < 3; a++)
+            mid[a] = (P.split_plane == HG_PLANE_CENTRE) ? model_bound(M, a, 2 * i[a] + 1, l[a] + 1)
+                                                        : lo[a] + 0.5 * (hi[a] - lo[a]);
     double S = 0.0, rmin = 0.0, rmax = 0.0;
     for (int32_t s = 0; s < P.n_ran; s++) {
         double x = lo[0] + unit_draw(key, 3ULL * s) * (hi[0] - lo[0]);
         double y = lo[1] + unit_draw(key, 3ULL * s + 1) * (hi[1] - lo[1]);
         double z = lo[2] + unit_draw(key, 3ULL * s + 2) * (hi[2] - lo[2]);
         double r = model_rho(M, x, y, z);
+        if (draws) {
+            draws[s].x[0] = x;
+            draws[s].x[1] = y;
+            draws[s].x[2] = z;
+            draws[s].r = r;
+            draws[s].s = s;
+        }
         S += r;
         if (s == 0 || r < rmin) rmin = r;
         if (s == 0 || r > rmax) rmax = r;

@@ -477,7 +477,8 @@ struct GridRays {
 // load, so lanes never wait for the longest path in their warp.
 //   OCC: resident blocks of 256 threads per SM the register budget is cut for
 //   (3: 80 registers; 4: 64 registers).
-template <int KIND, int MODE, int PREC, int OCC>
+//   NAV: 0 the grid's records hold neighbor-list heads, 1 ropes.
+template <int KIND, int MODE, int PREC, int OCC, int NAV>
 __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (A.run_if && *A.run_if == 0u) return;  // a fallback walk with nothing to do
@@ -535,32 +536,35 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.tau_int = A.tau_int;
     io.int_cell = A.int_cell;
     io.int_t = A.int_t;
-    walk_loop<KIND, MODE, PREC>(src, io, smem, A.n_smem);
+    walk_loop<KIND, MODE, PREC, NAV>(src, io, smem, A.n_smem);
 }
 
 // ------------------------------------------------------------------ launch plumbing
 
 typedef void (*KernelFn)(const TraceArgs);
 
-// Walking kernels by [kind][mode][prec][occupancy]; prec runs 0..1, and 0..3
-// for MODE_TAUADJ and MODE_TAUADJ_STAGE (optical depth and gradient precisions).
+// Walking kernels by [navigation][kind][mode][prec][occupancy]; prec runs
+// 0..1, and 0..3 for MODE_TAUADJ and MODE_TAUADJ_STAGE (optical depth and
+// gradient precisions).  Rope grids get their own instantiations, so that the
+// neighbor-list walk carries no code for ropes.
 constexpr int kModes = 7;
 inline int mode_precs(int m) {
     return (m == MODE_TAUADJ || m == MODE_TAUADJ_STAGE) ? 4 : (m == MODE_INTERACT ? 1 : 2);
 }
-KernelFn pick_kernel(int kind, int mode, int prec, int occ) {
-#define HG_K(K, M, P) {&trace_kernel<K, M, P, 3>, &trace_kernel<K, M, P, 4>}
-#define HG_M(K, M) {HG_K(K, M, 0), HG_K(K, M, 1), {nullptr, nullptr}, {nullptr, nullptr}}
-#define HG_MA(K, M) {HG_K(K, M, 0), HG_K(K, M, 1), HG_K(K, M, 2), HG_K(K, M, 3)}
-#define HG_M1(K, M) {HG_K(K, M, 0), {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}}
-    static const KernelFn table[2][kModes][4][2] = {
-        {HG_M(0, 0), HG_M(0, 1), HG_M(0, 2), HG_MA(0, 3), HG_M(0, 4), HG_MA(0, 5), HG_M1(0, 6)},
-        {HG_M(1, 0), HG_M(1, 1), HG_M(1, 2), HG_MA(1, 3), HG_M(1, 4), HG_MA(1, 5), HG_M1(1, 6)}};
+KernelFn pick_kernel(int kind, int mode, int prec, int occ, int nav) {
+#define HG_K(N, K, M, P) {&trace_kernel<K, M, P, 3, N>, &trace_kernel<K, M, P, 4, N>}
+#define HG_M(N, K, M) {HG_K(N, K, M, 0), HG_K(N, K, M, 1), {nullptr, nullptr}, {nullptr, nullptr}}
+#define HG_MA(N, K, M) {HG_K(N, K, M, 0), HG_K(N, K, M, 1), HG_K(N, K, M, 2), HG_K(N, K, M, 3)}
+#define HG_M1(N, K, M) {HG_K(N, K, M, 0), {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}}
+#define HG_KIND(N, K) {HG_M(N, K, 0), HG_M(N, K, 1), HG_M(N, K, 2), HG_MA(N, K, 3), HG_M(N, K, 4), HG_MA(N, K, 5), \
+                       HG_M1(N, K, 6)}
+    static const KernelFn table[2][2][kModes][4][2] = {{HG_KIND(0, 0), HG_KIND(0, 1)}, {HG_KIND(1, 0), HG_KIND(1, 1)}};
+#undef HG_KIND
 #undef HG_M1
 #undef HG_MA
 #undef HG_M
 #undef HG_K
-    return table[kind][mode][prec][occ == 4 ? 1 : 0];
+    return table[nav == HG_NAV_ROPES ? 1 : 0][kind][mode][prec][occ == 4 ? 1 : 0];
 }
 
 hg_status cuda_err(cudaError_t e, const char *what) {
@@ -626,12 +630,13 @@ constexpr int kSetupSmemMax = 200 * 1024 + kLatticeBytes;
 void set_smem_limits() {
     static std::once_flag once;
     std::call_once(once, [] {
-        for (int kd = 0; kd < 2; kd++)
-            for (int m = 0; m < kModes; m++)
-                for (int p = 0; p < mode_precs(m); p++)
-                    for (int oc = 3; oc <= 4; oc++)
-                        cudaFuncSetAttribute(pick_kernel(kd, m, p, oc), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+        for (int nav = 0; nav < 2; nav++)
+            for (int kd = 0; kd < 2; kd++)
+                for (int m = 0; m < kModes; m++)
+                    for (int p = 0; p < mode_precs(m); p++)
+                        for (int oc = 3; oc <= 4; oc++)
+                            cudaFuncSetAttribute(pick_kernel(kd, m, p, oc, nav),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         // the setup pass also stages the work lattice after the nodes
         cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemMax);
         cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemMax);
@@ -714,7 +719,7 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
     P.smem = (size_t)smem_nodes * node_bytes;
     int64_t blocks = 0;
-    const KernelFn k0 = pick_kernel(g->d.kind, MODE_TAU, HG_FP64, min_blocks);
+    const KernelFn k0 = pick_kernel(g->d.kind, MODE_TAU, HG_FP64, min_blocks, g->d.nav);
     hg_status hs = walk_blocks(k0, block, P.smem, n, blocks);
     if (hs != HG_OK) return hs;
     P.threads = blocks * block;
@@ -1021,7 +1026,7 @@ __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *
 hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t stream) {
     if (P.n == 0) return HG_OK;
     const hg_grid *g = P.g;
-    KernelFn k = pick_kernel(g->d.kind, mode, prec, P.min_blocks);
+    KernelFn k = pick_kernel(g->d.kind, mode, prec, P.min_blocks, g->d.nav);
     int64_t blocks = 0;
     hg_status hs = walk_blocks(k, P.block, P.smem, P.splitting ? INT64_MAX / 2 : P.n, blocks);
     if (hs != HG_OK) return hs;
@@ -1788,7 +1793,7 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
     A.dyn = (schedule == 2);
     A.starts = starts;
     A.counter = counter;
-    KernelFn k = pick_kernel(g->d.kind, MODE_TAU, prec, min_blocks);
+    KernelFn k = pick_kernel(g->d.kind, MODE_TAU, prec, min_blocks, g->d.nav);
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
     const size_t smem = (size_t)smem_nodes * node_bytes;
     cudaError_t e = cudaSuccess;

@@ -109,14 +109,15 @@ __device__ __forceinline__ bool in_axis(long long p, long long l, long long h, b
     return (l < p && p < h) || (p == l && !neg) || (p == h && (neg || (!pos && upper_face)));
 }
 
-// Top-down descent (Sect. 2.3) on keys.  The first n_smem nodes of the list
-// (the top levels, since the list is breadth first) come from shared memory.
+// Top-down descent (Sect. 2.3) on keys, from the root or from node start (a
+// rope's node).  The first n_smem nodes of the list (the top levels, since
+// the list is breadth first) come from shared memory.
 // KIND: HG_OCTREE, HG_KDTREE, or 2 = decided at run time from G.kind.
 template <int KIND>
 __device__ __forceinline__ int32_t descend(const DevGrid &G, const unsigned char *snodes, int n_smem, long long p0,
-                                           long long p1, long long p2, uint32_t sg) {
+                                           long long p1, long long p2, uint32_t sg, int32_t start = 0) {
     const bool kd = (KIND == 2) ? (G.kind == HG_KDTREE) : (KIND == HG_KDTREE);
-    int32_t nd = 0;
+    int32_t nd = start;
     for (int it = 0; it <= G.max_depth; it++) {
         if (kd) {
             longlong2 v;
@@ -495,15 +496,16 @@ __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Le
     *ax_out = ax;
     *tex_out = tex;
     if (ax < 0 || (SEGS && kt > S.ktstop)) return WALK_END;
-    if (L.first(2 * ax + (dpos(sg, ax) ? 1 : 0)) < 0) return WALK_END;  // exit wall on the domain boundary
+    if (L.first(2 * ax + (dpos(sg, ax) ? 1 : 0)) == -1) return WALK_END;  // exit wall on the domain boundary
     return WALK_GO;
 }
 
 // The next record to load and how to treat it.
-enum { CAND_ENTER = 0, CAND_TEST = 1 };
+enum { CAND_ENTER = 0, CAND_TEST = 1, CAND_ROPE = 2 };
 struct Cand {
-    int32_t id;     // record to load next
-    int32_t mode;   // CAND_ENTER: known to contain the exit point; CAND_TEST: a listed neighbor
+    int32_t id;     // record to load next (CAND_ROPE: the rope's internal node to search below)
+    int32_t mode;   // CAND_ENTER: known to contain the exit point; CAND_TEST: a listed neighbor (or a leaf a rope
+                    // leads to); CAND_ROPE: no record to load, locate the exit point below node id
     int32_t ax;     // exit axis
     int32_t e;      // next tail entry to try
     int32_t ntail;  // tail entries of the exit wall's list (-1: not read yet)
@@ -514,7 +516,10 @@ struct Cand {
 
 // After an exit through axis ax at time tex: the exit point (the wall on
 // the exit axis, o + d t clamped to the leaf on the others) and the first
-// neighbor to test, the head of the exit wall's list stored in the leaf.
+// neighbor to test, the head of the exit wall's list stored in the leaf --
+// or, on a grid loaded with ropes, the wall's rope: a leaf to test, or
+// (C.id <= -2) the internal node -2 - C.id to search below (cand_rope).
+template <int NAV>
 __device__ __forceinline__ void cand_first(const RayState &S, const Leaf &L, int ax, double tex, Cand &C) {
     const uint32_t sg = S.sg;
     const int w = 2 * ax + (dpos(sg, ax) ? 1 : 0);
@@ -529,8 +534,14 @@ __device__ __forceinline__ void cand_first(const RayState &S, const Leaf &L, int
     if (p1 > h1) p1 = h1;
     if (p2 < l2) p2 = l2;
     if (p2 > h2) p2 = h2;
-    C.id = L.first(w);
-    C.mode = CAND_TEST;
+    const int32_t f = L.first(w);
+    if (NAV == 0) {
+        C.id = f;
+        C.mode = CAND_TEST;
+    } else {
+        C.id = f < -1 ? -2 - f : f;
+        C.mode = f < -1 ? CAND_ROPE : CAND_TEST;
+    }
     C.ax = ax;
     C.e = 0;
     C.ntail = -1;
@@ -593,6 +604,22 @@ __device__ __forceinline__ int32_t cand_descend(const DevGrid &G, const unsigned
     const long long q1 = (ax == 1) ? wall : (b1 == 1 ? C.p1 : C.p2);
     const long long q2 = (ax == 2) ? wall : C.p2;
     return descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg);
+}
+
+// Rope walk: the leaf below the rope's internal node C.id that holds the
+// exit point (on the exit axis the far wall of the leaf being left, whose
+// bounds there are lo, hi; the clamped point on the others).  The caller then
+// tests that leaf like a listed neighbor.
+template <int KIND>
+__device__ __forceinline__ int32_t rope_descend(const DevGrid &G, const unsigned char *snodes, int n_smem, uint32_t sg,
+                                             long long lo, long long hi, const Cand &C) {
+    const int ax = C.ax;
+    const long long wall = dpos(sg, ax) ? hi : lo;
+    const int b1 = (ax == 0) ? 1 : 0;
+    const long long q0 = (ax == 0) ? wall : (b1 == 0 ? C.p1 : C.p2);
+    const long long q1 = (ax == 1) ? wall : (b1 == 1 ? C.p1 : C.p2);
+    const long long q2 = (ax == 2) ? wall : C.p2;
+    return descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg, C.id);
 }
 
 // Gradient scatter: a relaxed device-scope reduction (as atomicAdd without a
@@ -688,7 +715,8 @@ struct WalkIO {
 //   PREC (MODE_TAU/MODE_FILL): HG_FP64 or HG_FP32K.
 //   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
 //   PREC (MODE_TAUADJ): bit 0 the optical depth's (HG_FP32K), bit 1 the gradient's (FP32).
-template <int KIND, int MODE, int PREC, class Src>
+//   NAV: 0 the grids hold neighbor lists, 1 ropes, 2 either (read per grid).
+template <int KIND, int MODE, int PREC, int NAV, class Src>
 __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem) {
     constexpr bool SEGS = Src::kSegments;
     constexpr bool STAGE = (MODE == MODE_TAU_STAGE || MODE == MODE_TAUADJ_STAGE);
@@ -866,7 +894,18 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                 nc++;
             }
             if (r == WALK_GO) {
-                cand_first(S, L, ax, tex, C);
+                if (NAV == 0 || (NAV == 2 && G.nav == HG_NAV_NEIGHBOR_LISTS))
+                    cand_first<0>(S, L, ax, tex, C);
+                else
+                    cand_first<1>(S, L, ax, tex, C);
+                if (NAV != 0 && C.mode == CAND_ROPE) {  // a rope to an internal node: the exit point's leaf below it
+                    C.id = rope_descend<KIND>(G, snodes, n_smem, S.sg, L.lo(ax), L.hi(ax), C);
+                    C.mode = CAND_TEST;
+                    if (C.id < 0) {
+                        st = HG_RAY_LOST;
+                        goto finish;
+                    }
+                }
                 continue;
             }
         }

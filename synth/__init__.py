@@ -302,8 +302,10 @@ def workload_disk_1e6(kind: int, delta_max: Optional[float] = None):
     return model, bp, 1_000_000, seed
 
 
-def workload_torus_1e7(max_level: int = 12, delta_max: float = 1e-7):
-    """Ring torus + 1000 clumps, k-d tree under mass 1e-7, tau 0.5, q 0.9 (ratio 10)."""
+def workload_torus_1e7(max_level: int = 10, delta_max: float = 7e-7):
+    """Ring torus + 1000 clumps, k-d tree under the mass, optical-depth (tau 0.5) and dispersion (q 0.9,
+    density ratio 10) criteria.  Max level 10 with the mass threshold 7e-7 gives ~9.8e6 leaves; the
+    nominal mass threshold 1e-7 gives 8.4e6 leaves at max level 9 and 1.6e7 at max level 10."""
     seed = config_seed(3)
     model = make_torus(seed)
     bp = BuildParams(kind=TREE_KD, delta_max=delta_max, use_tau=True, tau_max=0.5,

@@ -68,6 +68,18 @@ CASES = [
                                                                       max_level=5, split_axis=1)),
     ("dyadic-kd-grad", lambda: synth.make_dyadic(4, level=3), dict(kind=1, delta_max=2e-3, use_q=True,
                                                                    q_max=0.5, max_level=5, split_axis=1)),
+    # split locations other than the centre (Sect. 2.2): explicit FP64 boxes
+    ("disk-oct-bary", lambda: synth.make_disk(), dict(kind=0, delta_max=1e-4, max_level=6, split_plane=1)),
+    ("disk-kd-mass", lambda: synth.make_disk(), dict(kind=1, delta_max=5e-5, max_level=6, split_plane=2)),
+    ("disk-kd-dens", lambda: synth.make_disk(), dict(kind=1, delta_max=5e-5, max_level=6, split_plane=3)),
+    ("torus-kd-mass-grad", lambda: synth.make_torus(11, n_clumps=60), dict(kind=1, delta_max=1e-3, use_tau=True,
+                                                                           tau_max=2.0, use_q=True, q_max=0.9,
+                                                                           max_level=5, split_axis=1,
+                                                                           split_plane=2)),
+    ("torus-oct-bary-q", lambda: synth.make_torus(12, n_clumps=30), dict(kind=0, delta_max=1e-2, use_q=True,
+                                                                         q_max=0.99, max_level=4, split_plane=1)),
+    ("dyadic-kd-dens", lambda: synth.make_dyadic(3, level=2), dict(kind=1, delta_max=1e-3, max_level=4,
+                                                                   split_plane=3)),
 ]
 
 
@@ -96,10 +108,13 @@ def _leaf_boxes(H):
     return H.node_lo[ln], H.node_hi[ln]
 
 
-@pytest.mark.parametrize("kind,split_axis", [(0, 0), (1, 0), (1, 1)], ids=["octree", "kd", "kd-gradient"])
-def test_neighbor_lists_tile_walls_and_are_symmetric(kind, split_axis):
+@pytest.mark.parametrize("kind,split_axis,split_plane", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 0, 1), (1, 0, 2),
+                                                          (1, 0, 3)],
+                         ids=["octree", "kd", "kd-gradient", "octree-bary", "kd-mass", "kd-dens"])
+def test_neighbor_lists_tile_walls_and_are_symmetric(kind, split_axis, split_plane):
     model = synth.make_disk()
-    H = hg.build_grid(model, synth.BuildParams(kind=kind, delta_max=3e-4, max_level=6, split_axis=split_axis))
+    H = hg.build_grid(model, synth.BuildParams(kind=kind, delta_max=3e-4, max_level=6, split_axis=split_axis,
+                                               split_plane=split_plane))
     lo, hi = _leaf_boxes(H)
     dlo, dhi = H.node_lo[0], H.node_hi[0]
     pairs = set()
@@ -121,7 +136,7 @@ def test_neighbor_lists_tile_walls_and_are_symmetric(kind, split_axis):
             np.testing.assert_array_equal(lo[ids, a] if s else hi[ids, a], plane)
             assert (np.diff(ov) <= 0).all()
             area = (hi[i, t[0]] - lo[i, t[0]]) * (hi[i, t[1]] - lo[i, t[1]])
-            assert ov.sum() == pytest.approx(area, rel=1e-15)
+            assert ov.sum() == pytest.approx(area, rel=1e-15 if split_plane == 0 else 1e-12)
             for j in ids:
                 pairs.add((i, w, int(j)))
     for (i, w, j) in pairs:
@@ -171,6 +186,15 @@ def test_load_grid_rejects_corrupt_descriptions(small_host, what):
     desc = _corrupt(_desc(small_host), what)
     with pytest.raises(hg.HgError, match="grid description invalid"):
         hg.load_grid(desc, validate=True)
+
+
+def test_builder_rejects_split_plane_of_the_other_tree_kind():
+    with pytest.raises(hg.HgError, match="split_plane"):
+        hg.build_grid(synth.make_disk(), synth.BuildParams(kind=0, split_plane=2))
+    with pytest.raises(hg.HgError, match="split_plane"):
+        hg.build_grid(synth.make_disk(), synth.BuildParams(kind=1, split_plane=1))
+    with pytest.raises(hg.HgError, match="split_plane"):
+        hg.build_grid(synth.make_disk(), synth.BuildParams(kind=1, split_plane=4))
 
 
 def test_builder_rejects_bad_split_axis():
@@ -226,3 +250,79 @@ def test_tau_max_recipe_known_quantile_matches_oracle(kind):
     for frac in (0.9, 0.89, 0.92, 0.0, 1.0):
         assert hg.tau_max_recipe(m, bp, fraction=frac, threads=2) == oracle.tau_max_recipe(m, bp, fraction=frac)
     assert hg.tau_max_recipe(m, bp) == pytest.approx(4.0 * 1.5 * math.sqrt(3.0) * 0.5, rel=4e-16)
+
+
+# ----------------------------------------------------------------------------- ropes
+
+def _depths(H):
+    d = np.zeros(H.n_nodes, np.int64)
+    nch = 8 if H.kind == 0 else 2
+    for nd in range(H.n_nodes):
+        c = H.child_first[nd]
+        if c >= 0:
+            d[c:c + nch] = d[nd] + 1
+    return d
+
+
+@pytest.mark.parametrize("kind,split_plane", [(0, 0), (1, 0), (0, 1), (1, 2)],
+                         ids=["octree", "kd", "octree-bary", "kd-mass"])
+def test_ropes_are_the_deepest_covering_nodes(kind, split_plane):
+    # brute force over every node: the nodes across a leaf wall that cover its whole face are nested, and the
+    # rope is the deepest of them; the leaves below it that touch the face are exactly the wall's neighbor list
+    H = hg.build_grid(synth.make_disk(), synth.BuildParams(kind=kind, delta_max=2e-3, max_level=5,
+                                                           split_plane=split_plane))
+    assert 300 < H.n_leaves < 3000
+    R = hg.build_ropes(H, threads=3)
+    np.testing.assert_array_equal(R, hg.build_ropes(H, threads=1))
+    lo, hi = H.node_lo, H.node_hi
+    depth = _depths(H)
+    dlo, dhi = lo[0], hi[0]
+    n_internal = 0
+    for i in range(H.n_leaves):
+        ln = H.leaf_node[i]
+        for w in range(6):
+            a, s = w // 2, w % 2
+            P = hi[ln, a] if s else lo[ln, a]
+            r = R[i, w]
+            if P == (dhi[a] if s else dlo[a]):
+                assert r == -1
+                continue
+            across = (lo[:, a] <= P) & (P < hi[:, a]) if s else (lo[:, a] < P) & (P <= hi[:, a])
+            cover = across.copy()
+            for b in range(3):
+                if b != a:
+                    cover &= (lo[:, b] <= lo[ln, b]) & (hi[ln, b] <= hi[:, b])
+            nodes = np.nonzero(cover)[0]
+            deepest = nodes[np.argmax(depth[nodes])]
+            assert (depth[nodes] == depth[deepest]).sum() == 1
+            node = H.leaf_node[r] if r >= 0 else -2 - r
+            assert node == deepest
+            n_internal += r <= -2
+            # the rope's node touches the wall from the far side
+            assert (lo[node, a] if s else hi[node, a]) == P
+            # leaves below it touching the face = the neighbor list
+            below = set()
+            stack = [node]
+            while stack:
+                nd = stack.pop()
+                if H.child_first[nd] < 0:
+                    j = H.node_leaf[nd]
+                    ok = (lo[nd, a] == P) if s else (hi[nd, a] == P)
+                    for b in range(3):
+                        if b != a:
+                            ok = ok and min(hi[nd, b], hi[ln, b]) > max(lo[nd, b], lo[ln, b])
+                    if ok:
+                        below.add(int(j))
+                else:
+                    stack.extend(range(H.child_first[nd], H.child_first[nd] + (8 if kind == 0 else 2)))
+            lst = set(H.nbr_id[H.nbr_off[6 * i + w]:H.nbr_off[6 * i + w + 1]].tolist())
+            assert below == lst
+    assert n_internal > 0
+
+
+def test_build_ropes_rejects_bad_leaf_ids():
+    H = hg.build_grid(synth.make_disk(), synth.BuildParams(kind=1, delta_max=2e-3, max_level=4))
+    d = _desc(H)
+    d.node_leaf[d.node_leaf >= 0] = 0
+    with pytest.raises(hg.HgError):
+        hg.build_ropes(d)

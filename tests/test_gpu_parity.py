@@ -93,6 +93,54 @@ def test_gradient_axis_kd_sequences_bit_exact(hg, shape):
     assert ref["ncross"].sum() > 4000 * 5
 
 
+SPLIT_VARIANTS = [(synth.TREE_OCTREE, synth.PLANE_BARYCENTRE, 0, 1e-4), (synth.TREE_KD, synth.PLANE_EQUAL_MASS, 0, 5e-5),
+                  (synth.TREE_KD, synth.PLANE_EQUAL_DENSITY, 0, 5e-5), (synth.TREE_KD, synth.PLANE_EQUAL_MASS, 1, 5e-5)]
+SPLIT_IDS = ["octree-barycentre", "kd-equal-mass", "kd-equal-density", "kd-gradient-equal-mass"]
+
+
+def _wall_rays(tree, seed, n):
+    """Rays starting on the tree's own (non-dyadic) leaf walls, edges and corners, half of them along
+    axis-aligned or in-plane directions (zero components), the rest isotropic."""
+    rng = np.random.default_rng(seed)
+    leaves = rng.integers(0, tree.n_leaves, n)
+    lo, hi = tree.leaf_lo[leaves], tree.leaf_hi[leaves]
+    p = lo + rng.random((n, 3)) * (hi - lo)
+    pick = rng.random((n, 3))
+    p = np.where(pick < 0.35, lo, np.where(pick < 0.7, hi, p))
+    k = synth.isotropic_dirs(rng, n)
+    m = rng.random(n) < 0.5
+    kd = rng.choice([-1.0, -0.0, 0.0, 1.0, 0.6, -0.8], size=(n, 3))
+    bad = np.all(kd == 0, axis=1)
+    kd[bad, 0] = 1.0
+    k[m] = kd[m]
+    return p, k
+
+
+@pytest.mark.parametrize("kind,plane,axis,dmax", SPLIT_VARIANTS, ids=SPLIT_IDS)
+@pytest.mark.parametrize("shape", [dict(), dict(split="force"), dict(schedule=1, smem_nodes=0)],
+                         ids=["auto", "forced-split", "static-nosmem"])
+def test_split_location_variants_sequences_bit_exact(hg, kind, plane, axis, dmax, shape):
+    # barycentric octrees and equal-mass / equal-mean-density k-d trees (Sect. 2.2): node boxes with FP64
+    # planes that are no dyadic lattice points, walked through their FP64-keyed leaf records; cell
+    # sequences, lengths, counts and statuses bit-exact against the oracle, tau within 1e-6 (FP64) / 1e-5
+    model, bp, n_rays, seed = synth.workload_disk_small()
+    bp.kind, bp.split_plane, bp.split_axis, bp.delta_max = kind, plane, axis, dmax
+    H = hg.build_grid(model, bp)
+    T = oracle.build_tree(model, bp)
+    np.testing.assert_array_equal(H.child_first, T.child)
+    np.testing.assert_array_equal(H.node_lo, T.lo)
+    np.testing.assert_array_equal(H.node_hi, T.hi)
+    grid = hg.load_grid(H, validate=True)
+    o, k = synth.emission_rays(seed + 11, 4000)
+    ref, _ = _compare(hg, grid, T, o, k, **shape)
+    assert ref["ncross"].sum() > 4000 * 5
+    _compare(hg, grid, T, o, k, precision="fp32k", **shape)
+    a, d, L = synth.endpoint_paths(seed + 12, 2000)
+    _compare(hg, grid, T, a, d, smax=L, kappa=1.7, **shape)
+    wo, wk = _wall_rays(T, seed + 13, 3000)
+    _compare(hg, grid, T, wo, wk, **shape)
+
+
 SHAPES = [dict(), dict(schedule=1), dict(schedule=2, block=128, smem_nodes=0), dict(schedule=3, block=256, smem_nodes=64),
           dict(schedule=1, block=64, smem_nodes=100000), dict(min_blocks=4), dict(min_blocks=4, schedule=1, block=96)]
 
@@ -600,6 +648,112 @@ def test_interaction_points_path_ends_and_bad_inputs(hg, disk_grids, kind):
     _same_interactions(hg, grid, tree, o, kk, rng.exponential(0.1, 2000))
 
 
+# ----------------------------------------------------------------------------- ropes
+# The rope walk (hg_load_grid_ropes): the next leaf from the exit wall's rope, located below the rope's node
+# when that is not a leaf, instead of from the neighbor list.  Same contract, so the same oracle.
+
+@pytest.fixture(scope="module")
+def rope_grids(hg, disk_grids):
+    model, grids, o, k = disk_grids
+    out = {}
+    for kind in (0, 1):
+        _, tree, H = grids[kind]
+        G = hg.load_grid(H, validate=True, nav="ropes")
+        assert G.nav == hg.NAV_ROPES and G.n_tail == 1
+        out[kind] = (G, tree, H)
+    return out
+
+
+ROPE_SHAPES = [dict(), dict(schedule=1, smem_nodes=0), dict(split="force"), dict(schedule=2, block=128),
+               dict(min_blocks=4)]
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+@pytest.mark.parametrize("shape", ROPE_SHAPES, ids=[str(s) for s in ROPE_SHAPES])
+def test_rope_walk_sequences_bit_exact(hg, disk_grids, rope_grids, kind, shape):
+    model, grids, o, k = disk_grids
+    G, tree, H = rope_grids[kind]
+    ref, _ = _compare(hg, G, tree, o, k, **shape)
+    assert ref["ncross"].sum() > 0
+    _compare(hg, G, tree, o, k, precision="fp32k", **shape)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_rope_walk_path_ends_degenerate_rays_and_interactions(hg, rope_grids, kind):
+    G, tree, H = rope_grids[kind]
+    a, d, L = synth.endpoint_paths(78, 3001)
+    _compare(hg, G, tree, a, d, smax=L, kappa=2.5)
+    wo, wk = _wall_rays(tree, 79 + kind, 4000)
+    _compare(hg, G, tree, wo, wk)
+    _compare(hg, G, tree, wo, wk, split="force")
+    o, k = synth.emission_rays(80, 3000)
+    ti = np.random.default_rng(kind).exponential(2.0, 3000)
+    _same_interactions(hg, G, tree, o, k, ti, kappa=3.0)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_rope_walk_degenerate_rays_on_adaptive_grid(hg, kind):
+    model = synth.make_torus(21, n_clumps=20)
+    bp = synth.BuildParams(kind=kind, delta_max=1e-3, use_q=True, q_max=0.9, max_level=5)
+    H = hg.build_grid(model, bp)
+    grid = hg.load_grid(H, nav="ropes", ropes=hg.build_ropes(H))
+    tree = oracle.build_tree(model, bp)
+    o, k = synth.degenerate_rays(levels=5, n_random=3000, seed=kind + 9)
+    _compare(hg, grid, tree, o, k)
+    _compare(hg, grid, tree, o, k, split="force", smem_nodes=0)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_rope_walk_emission_and_adjoint(hg, disk_grids, rope_grids, kind):
+    model, grids, o, k = disk_grids
+    G, tree, H = rope_grids[kind]
+    w = synth.adjoint_weights(81, o.shape[0])
+    ref = oracle.trace(tree, o, k, emit=True)
+    gr = oracle.adjoint(tree.n_leaves, ref["seg_off"], ref["seg_cell"], ref["seg_ds"], w.astype(np.float64))
+    O, K, W = _cuda(o), _cuda(k), _cuda(w, torch.float32)
+    R = hg.prepare_rays(G, O, K, split="force")
+    sp = R.emit_single_pass(w=W, grad_precision="fp64")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(_np(sp["seg_off"]), ref["seg_off"])
+    np.testing.assert_array_equal(_np(sp["seg_cell"]), ref["seg_cell"])
+    np.testing.assert_array_equal(_np(sp["seg_ds"]), ref["seg_ds"])
+    np.testing.assert_allclose(_np(sp["grad"]), gr, rtol=1e-12, atol=0)
+    R.free()
+    g = hg.tau_gradient(G, O, K, W, grad_precision="fp64")
+    np.testing.assert_allclose(_np(g), gr, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("kind,plane,axis,dmax", SPLIT_VARIANTS, ids=SPLIT_IDS)
+def test_rope_walk_on_split_location_variants(hg, kind, plane, axis, dmax):
+    model, bp, n_rays, seed = synth.workload_disk_small()
+    bp.kind, bp.split_plane, bp.split_axis, bp.delta_max = kind, plane, axis, dmax
+    H = hg.build_grid(model, bp)
+    T = oracle.build_tree(model, bp)
+    G = hg.load_grid(H, validate=True, nav="ropes")
+    o, k = synth.emission_rays(seed + 21, 4000)
+    _compare(hg, G, T, o, k)
+    wo, wk = _wall_rays(T, seed + 22, 3000)
+    _compare(hg, G, T, wo, wk, split="force")
+
+
+def test_rope_and_list_grids_in_one_batch_match_oracle(hg):
+    grids, trees, begins = _uneven_batch(hg, ropes=True)
+    assert {g.nav for g in grids} == {hg.NAV_NEIGHBOR_LISTS, hg.NAV_ROPES}
+    n = begins[-1]
+    o, k = synth.emission_rays(synth.config_seed(4) + 15, n)
+    b = hg.Batch(grids, begins)
+    O, K = _cuda(o), _cuda(k)
+    for prec, rtol in (("fp64", TAU_RTOL_FP64), ("fp32k", TAU_RTOL_FP32K)):
+        tau, nc, st = b.trace(O, K, kappa=1.4, precision=prec)
+        torch.cuda.synchronize()
+        for i, t in enumerate(trees):
+            s = slice(begins[i], begins[i + 1])
+            ref = oracle.trace(t, o[s], k[s], kappa=1.4)
+            np.testing.assert_array_equal(_np(nc[s]), ref["ncross"])
+            np.testing.assert_array_equal(_np(st[s]), ref["status"])
+            _check_tau(_np(tau[s]), ref["tau"], rtol)
+
+
 # ----------------------------------------------------------------------------- batching and tuning
 
 def test_batch_matches_single_grid_launches(hg):
@@ -626,10 +780,11 @@ def test_batch_matches_single_grid_launches(hg):
             np.testing.assert_array_equal(_np(st[s]), _np(s1))
 
 
-def _uneven_batch(hg):
+def _uneven_batch(hg, ropes=False):
     """Seven grids of uneven size for the batched launch: octree and k-d tree of each of the disk,
     the clump-free ring and the ring with clumps (seeded parameters), one more disk octree, and one
-    grid that gets no rays; ray counts from 0 to ~2e4."""
+    grid that gets no rays; ray counts from 0 to ~2e4.  ropes: every other grid loaded for the rope
+    walk."""
     rng = np.random.default_rng(synth.config_seed(4) + 101)
     specs = []
     for kind in (synth.TREE_OCTREE, synth.TREE_KD):
@@ -652,7 +807,7 @@ def _uneven_batch(hg):
         target = float(np.exp(rng.uniform(np.log(2e3), np.log(4e4))))
         bp = synth.BuildParams(kind=kind, delta_max=1.0 / target, max_level=7, seed=sub)
         H = hg.build_grid(model, bp)
-        grids.append(hg.load_grid(H))
+        grids.append(hg.load_grid(H, nav="ropes" if ropes and len(grids) % 2 else "lists"))
         trees.append(oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho))
         begins.append(begins[-1] + nr)
     return grids, trees, begins
@@ -745,14 +900,16 @@ def disk_1e6(hg):
         np.testing.assert_array_equal(H.child_first, T.child)
         np.testing.assert_array_equal(H.leaf_rho, T.leaf_rho)
         out[kind] = (hg.load_grid(H), T)
+        out[kind + 2] = (hg.load_grid(H, nav="ropes"), T)
     o, k = synth.emission_rays(seed, n_rays)
     return model, out, o, k
 
 
+@pytest.mark.parametrize("nav", ["lists", "ropes"])
 @pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
-def test_disk_1e6_leaves_1e6_rays(hg, disk_1e6, kind):
+def test_disk_1e6_leaves_1e6_rays(hg, disk_1e6, kind, nav):
     model, grids, o, k = disk_1e6
-    grid, tree = grids[kind]
+    grid, tree = grids[kind + (2 if nav == "ropes" else 0)]
     O, K = _cuda(o), _cuda(k)
     ref = oracle.trace(tree, o, k)
     for prec in ("fp64", "fp32k"):
@@ -782,14 +939,14 @@ def test_single_leaf_grid(hg):
 
 @pytest.fixture(scope="module")
 def torus_full(hg):
-    model, bp, n_rays, seed = synth.workload_torus_1e7(max_level=9)
+    model, bp, n_rays, seed = synth.workload_torus_1e7()
     H = hg.build_grid(model, bp)
     return model, bp, H, seed
 
 
 def test_torus_full_size_builder_decisions_sampled(hg, torus_full):
     model, bp, H, seed = torus_full
-    assert 7e6 < H.n_leaves < 1.2e7
+    assert 9e6 < H.n_leaves < 1.1e7
     rng = np.random.default_rng(1)
     leaves = H.leaf_node[rng.choice(H.n_leaves, 300, replace=False)]
     parent = np.full(H.n_nodes, -1, np.int64)
