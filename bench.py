@@ -52,6 +52,12 @@ BYTES_PER_RAY = {"fp64": 48 + 8 + 4 + 1, "fp32k": 48 + 4 + 4 + 1}
 STAGE_BYTES_PER_CROSSING = {"fp64": 4 + 8, "fp32k": 4 + 4}
 STAGE_BYTES_PER_RAY = 4
 L2_FLUSH_BYTES = 512 << 20
+# what bounds the walk besides the copy bandwidth (see DESIGN, GB300-specific choices 1 and 4): random
+# gathers of 96-byte records from a 2 GB array sustained 13.2 G records/s (~1.27 TB/s) in a separate probe,
+# and FP64 add / multiply ran at ~500 G instructions/s; the FP64 walk issues 13 FP64 instructions per crossing
+RANDOM_GATHER_GBS = 1.27e3
+FP64_OPS_PER_S = 500e9
+FP64_OPS_PER_CROSSING = {"fp64": 13, "fp32k": 12}
 
 
 # ----------------------------------------------------------------------------- distributed plumbing
@@ -201,20 +207,18 @@ def make_small_grids(hg, threads=0):
 
 
 def make_torus_grid(hg, threads=0):
-    model, bp, n_rays, seed = synth.workload_torus_1e7(max_level=TORUS_MAX_LEVEL)
+    model, bp, n_rays, seed = synth.workload_torus_1e7()
     t0 = time.time()
     host = hg.build_grid(model, bp, threads=threads)
     return model, [dict(name="kd", kind=1, host=host, build_s=time.time() - t0)], n_rays, seed
 
 
-# max level of the torus workload: 9 gives 8.4e6 leaves (10 would give ~3e7)
-TORUS_MAX_LEVEL = 9
 
 WORKLOADS = {
     "disk-1e6": ("disk, octree (mass 1e-6, max level 12) and k-d tree (same threshold), 1e6 rays per grid",
                  make_disk_grids),
     "disk-1e4": ("disk, octree and k-d tree (mass 1e-4, max level 6), 1e4 rays per grid", make_small_grids),
-    "torus-1e7": ("ring torus + 1000 clumps, k-d tree (mass 1e-7, tau 0.5, q 0.9, max level 9, ~8.4e6 leaves), "
+    "torus-1e7": ("ring torus + 1000 clumps, k-d tree (mass 7e-7, tau 0.5, q 0.9, max level 10, ~9.8e6 leaves), "
                   "1e7 rays: FP32-Kahan and FP64 passes plus the adjoint", make_torus_grid),
     "batch-64": ("64 grids (octree/k-d, disk/ring/clumps, seeded), 1e5-1e7 rays each, one persistent launch",
                  None),
@@ -369,6 +373,7 @@ def run_ours(args):
                 c0.record(gs)
             cell, ds, _ = R.emit_staged_gradient(off, W, kappa=1.0, grad=g["grad"], grad_precision="fp32",
                                                  capacity=cap, status=g["st"])
+            g["off"], g["cell"], g["ds"] = off, cell, ds
             if record:
                 c1.record(gs)
                 cev.append((g["name"], c0, c1))
@@ -456,21 +461,45 @@ def run_ours(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = tot_bytes / (tot_time / 1e3) / 1e9
     traffic = recorded_traffic(args.workload, prec)
+    tot_cross = sum(int(g["nc"].sum().item()) for g in grids)
+    byte_per_cross = tot_bytes / max(1, tot_cross)
+    fp64_gcross = FP64_OPS_PER_S / FP64_OPS_PER_CROSSING[prec]
     roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s", frac=round(achieved / peak, 4),
                     traffic=traffic, kernel="trace_kernel, one walk for optical depth and staged emission over "
                                             "prepared rays (hg_rays_trace_stage)",
-                    peak_source="measured" if "hbm_gbs" in peaks else "fallback")
+                    peak_source="measured" if "hbm_gbs" in peaks else "fallback",
+                    ceilings=dict(
+                        achieved_gcross_per_s=round(tot_cross / tot_time / 1e6, 2),
+                        fp64_issue_gcross_per_s=round(fp64_gcross / 1e9, 1),
+                        fp64_issue_frac_of_peak=round(fp64_gcross * byte_per_cross / 1e9 / peak, 3),
+                        random_gather_gbs=RANDOM_GATHER_GBS,
+                        random_gather_frac_of_peak=round(RANDOM_GATHER_GBS / peak, 3),
+                        note=f"{FP64_OPS_PER_CROSSING[prec]} FP64 instructions per crossing at the ~500 G/s this GPU "
+                             "issues them bound the walk at fp64_issue_gcross_per_s, i.e. fp64_issue_frac_of_peak "
+                             "of the copy bandwidth in algorithmic bytes; random 96-byte record gathers from "
+                             "beyond L2 sustain random_gather_gbs (separate probes); L2 serves part of the records"))
 
-    # e2e: the same step through the public API with host buffers (pinned), copies inside the timed region
+    # the emitted cell sequences of the last step, on the host (the navigation comparison reads a sample)
+    for g in grids:
+        g["seg_off_h"] = g["off"].cpu().numpy()
+        g["seg_cell_h"] = g["cell"].cpu().numpy()
+
+    # e2e: the same step through the public API with host buffers (pinned), copies inside the timed region:
+    # rays in; tau, crossing counts, the emitted cells and lengths (the CSR) and the gradient out
     e2e = None
     if not args.no_e2e:
         ho = torch.tensor(o).pin_memory()
         hk = torch.tensor(k).pin_memory()
-        htau = [torch.empty(n_rays, dtype=g["tau"].dtype).pin_memory() for g in grids]
-        hnc = [torch.empty(n_rays, dtype=torch.int32).pin_memory() for g in grids]
+        hout = []
+        for g in grids:
+            hout.append([torch.empty(n_rays, dtype=g["tau"].dtype).pin_memory(),
+                         torch.empty(n_rays, dtype=torch.int32).pin_memory(),
+                         torch.empty(n_rays + 1, dtype=torch.int64).pin_memory(),
+                         torch.empty(g["cap"], dtype=torch.int32).pin_memory(),
+                         torch.empty(g["cap"], dtype=g["ds"].dtype).pin_memory(),
+                         torch.empty(g["grid"].n_leaves, dtype=torch.float32).pin_memory()])
         barrier(dist, dev)
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         es = []
         for s in range(args.steps):
             flush.zero_()
@@ -479,18 +508,20 @@ def run_ours(args):
             O.copy_(ho, non_blocking=True)
             K.copy_(hk, non_blocking=True)
             step()
-            for j, g in enumerate(grids):
-                htau[j].copy_(g["tau"], non_blocking=True)
-                hnc[j].copy_(g["nc"], non_blocking=True)
+            for h, g in zip(hout, grids):
+                for dst, src in zip(h, (g["tau"], g["nc"], g["off"], g["cell"], g["ds"], g["grad"])):
+                    dst.copy_(src[:dst.shape[0]], non_blocking=True)
             b.record(stream)
             es.append((a, b))
         torch.cuda.synchronize()
         barrier(dist, dev)
         e_ms = max_over_ranks(dist, sum(x.elapsed_time(y) for x, y in es), dev)
         h2d = 2 * n_rays * 3 * 8
-        d2h = sum(n_rays * (g["tau"].element_size() + 4) for g in grids)
+        d2h = sum(sum(t.numel() * t.element_size() for t in h) for h in hout)
         e2e = dict(value=sum_over_ranks(dist, rays_per_step * args.steps, dev) / (e_ms / 1e3), unit=UNIT,
-                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                   copied="in: origins, directions; out per grid: tau, crossing counts, CSR offsets, "
+                          "emitted cells and lengths, gradient")
 
     # quality at equal cell counts (outside the timed region): a k-d tree whose mass threshold is bisected
     # until its leaf count is within 5 % of the octree's, with its Delta-rho and Delta-tau
@@ -501,9 +532,24 @@ def run_ours(args):
     if world == 1 and args.kd_orientations and args.workload == "disk-1e6":
         orient = kd_orientations(hg, torch, model, O, K, P, PA, PK, PL, RT, TT, flush, stream)
 
+    # the benchmark spec's other configurations, after the timed step (single GPU)
+    extras = {}
+    torus_check = None
+    if world == 1 and not args.no_extras and args.workload == "disk-1e6":
+        for g in grids:
+            g["R"] = None
+        extras["torus_1e7"], torus_check = measure_torus(hg, torch, dev, flush, stream)
+        torch.cuda.empty_cache()
+        extras["batch_64"] = measure_batch(hg, torch, dev, flush, stream)
+        torch.cuda.empty_cache()
+        extras["navigation"] = measure_navigation(hg, torch, grids, O, K, flush, stream)
+        extras["interaction"] = measure_interaction(hg, torch, grids, O, K, rs, flush, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(model, grids, o, k, pts, pa, pk, pl, w, sample=args.cpu_sample)
+        if torus_check is not None:
+            extras["torus_1e7"]["vs_oracle"] = torus_oracle_check(*torus_check)
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=tot_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -511,7 +557,7 @@ def run_ours(args):
                 config=dict(workload=args.workload, description=desc, rays_per_grid=n_rays, points=n_pts,
                             paths=n_paths, precision=prec, l2="flushed between steps (512 MB write)",
                             grids=kern, kd_matched_to_octree=matched,
-                            **({"kd_orientations": orient} if orient else {})),
+                            **({"kd_orientations": orient} if orient else {}), **extras),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
                 clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"]))
     if rank == 0:
@@ -542,6 +588,262 @@ def _peak():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- sub-workloads of the default line
+# Measured after the timed disk step (outside it) and reported under config: the benchmark spec's other
+# configurations -- the ~1e7-leaf torus (FP32-Kahan against FP64), the 64-grid batch (one graph-replayed
+# launch against 64 launches), the rope walk against the neighbor-list walk, the interaction search.
+
+def _events_ms(torch, stream, reps, flush, fn):
+    return statistics.median(_timed_steps(torch, stream, reps, flush, fn))
+
+
+def measure_torus(hg, torch, dev, flush, stream, reps=3):
+    """The ~1e7-leaf k-d tree of the ring torus with clumps, 1e7 rays: one-shot FP32-Kahan and FP64 passes,
+    the FP32 adjoint; rays/s, crossings/s, roofline per pass, FP32K against FP64 tau."""
+    model, bp, n_rays, seed = synth.workload_torus_1e7()
+    t0 = time.time()
+    H = hg.build_grid_gpu(model, bp)
+    build_s = time.time() - t0
+    G = hg.load_grid(H)
+    o, k = synth.emission_rays(seed, n_rays)
+    w = synth.adjoint_weights(seed + 3, n_rays)
+    O, K, W = torch.tensor(o, device=dev), torch.tensor(k, device=dev), torch.tensor(w, device=dev)
+    t32 = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    t64 = torch.empty(n_rays, dtype=torch.float64, device=dev)
+    nc32 = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    nc = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    st = torch.empty(n_rays, dtype=torch.uint8, device=dev)
+    grad = torch.zeros(G.n_leaves, dtype=torch.float32, device=dev)
+    run = {"fp32k": lambda: hg.trace_rays(G, O, K, precision="fp32k", out=(t32, nc32, st)),
+           "fp64": lambda: hg.trace_rays(G, O, K, precision="fp64", out=(t64, nc, st))}
+    for f in run.values():
+        f()
+    bits = int(hg.reduce_status(st).item())
+    peak, _ = _peak()
+    cr = int(nc.sum().item())
+    passes = {}
+    for prec, f in run.items():
+        ms = _events_ms(torch, stream, reps, flush, f)
+        byt = BYTES_PER_CROSSING[prec] * cr + BYTES_PER_RAY[prec] * n_rays
+        passes[prec] = dict(trace_ms=round(ms, 3), rays_per_s=n_rays / ms * 1e3, gcross_per_s=cr / ms / 1e6,
+                            achieved_gbs=round(byt / (ms / 1e3) / 1e9, 1),
+                            roofline_frac=round(byt / (ms / 1e3) / 1e9 / peak, 4))
+    grad_ms = _events_ms(torch, stream, 1, flush, lambda: (grad.zero_(), hg.tau_gradient(
+        G, O, K, W, grad=grad, grad_precision="fp32")))
+    a32 = t32.double().cpu().numpy()
+    a64 = t64.cpu().numpy()
+    pos = a64 > 0
+    rel = np.abs(a32[pos] - a64[pos]) / a64[pos]
+    out = dict(leaves=G.n_leaves, rays=n_rays, mean_ncross=cr / n_rays, build_gpu_s=round(build_s, 2),
+               status_bits=bits, passes=passes, adjoint_fp32_ms=round(grad_ms, 3),
+               fp32k_over_fp64_speed=passes["fp64"]["trace_ms"] / passes["fp32k"]["trace_ms"],
+               fp32k_vs_fp64=dict(max_rel=float(rel.max()), median_rel=float(np.median(rel)),
+                                  identical_counts=bool(torch.equal(nc, nc32))),
+               description="ring torus + 1000 clumps, k-d tree (mass 7e-7, tau 0.5, q 0.9, max level 10), "
+                           "built on the GPU; 1e7 emission rays, one-shot hg_trace_rays per precision")
+    del O, K, W, grad
+    return out, (H, o, k, a64, a32)
+
+
+def measure_batch(hg, torch, dev, flush, stream, reps=3):
+    """64 grids of uneven size (octree / k-d, disk / ring / clumps), ~1.5e8 rays: the batched FP32-Kahan
+    launch replayed from a CUDA graph against 64 separate FP64 launches (and FP32K, and batched FP64)."""
+    specs = synth.batch_specs(64)
+    grids, begins, leaves = [], [0], []
+    t0 = time.time()
+    for sp in specs:
+        bp = synth.BuildParams(kind=sp["kind"], delta_max=2.0 / sp["target_leaves"], max_level=10, seed=sp["seed"])
+        grids.append(hg.load_grid(hg.build_grid_gpu(sp["model"], bp)))
+        leaves.append(grids[-1].n_leaves)
+        begins.append(begins[-1] + sp["n_rays"])
+    build_s = time.time() - t0
+    total = begins[-1]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.config_seed(4))
+    O = torch.rand(total, 3, dtype=torch.float64, device=dev, generator=gen) * 2.0 - 1.0
+    mu = torch.rand(total, dtype=torch.float64, device=dev, generator=gen) * 2.0 - 1.0
+    phi = torch.rand(total, dtype=torch.float64, device=dev, generator=gen) * (2.0 * math.pi)
+    sn = torch.sqrt(torch.clamp(1.0 - mu * mu, min=0.0))
+    K = torch.stack([sn * torch.cos(phi), sn * torch.sin(phi), mu], dim=1).contiguous()
+    del mu, phi, sn
+    batch = hg.Batch(grids, begins)
+    t32 = torch.empty(total, dtype=torch.float32, device=dev)
+    t64 = torch.empty(total, dtype=torch.float64, device=dev)
+    nc = torch.empty(total, dtype=torch.int32, device=dev)
+    st = torch.empty(total, dtype=torch.uint8, device=dev)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batch.trace(O, K, precision="fp32k", out=(t32, nc, st))
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.trace(O, K, precision="fp32k", out=(t32, nc, st))
+    graph.replay()
+    torch.cuda.synchronize()
+    bits = int(hg.reduce_status(st).item())
+    cr = int(nc.sum().item())
+
+    def sep(prec, out):
+        for i, g in enumerate(grids):
+            s_ = slice(begins[i], begins[i + 1])
+            hg.trace_rays(g, O[s_], K[s_], precision=prec, out=(out[0][s_], out[1][s_], None))
+
+    batched = _events_ms(torch, stream, reps, flush, graph.replay)
+    sep64 = _events_ms(torch, stream, reps, flush, lambda: sep("fp64", (t64, nc)))
+    sep32 = _events_ms(torch, stream, reps, flush, lambda: sep("fp32k", (t32, nc)))
+    b64 = _events_ms(torch, stream, reps, flush, lambda: batch.trace(O, K, precision="fp64", out=(t64, nc, None)))
+    peak, _ = _peak()
+    byt = BYTES_PER_CROSSING["fp32k"] * cr + BYTES_PER_RAY["fp32k"] * total
+    del graph, batch, O, K
+    return dict(grids=len(grids), rays=total, leaves_total=int(sum(leaves)), leaves_min=int(min(leaves)),
+                leaves_max=int(max(leaves)), build_gpu_s=round(build_s, 1), mean_ncross=cr / total, status_bits=bits,
+                batched_fp32k_graph_ms=round(batched, 3), batched_fp32k_rays_per_s=total / batched * 1e3,
+                separate_fp64_ms=round(sep64, 3), separate_fp64_rays_per_s=total / sep64 * 1e3,
+                separate_fp32k_ms=round(sep32, 3), batched_fp64_ms=round(b64, 3),
+                batched_fp32k_over_separate_fp64=sep64 / batched, batched_fp32k_over_separate_fp32k=sep32 / batched,
+                roofline_frac_batched_fp32k=round(byt / (batched / 1e3) / 1e9 / peak, 4),
+                rays_generated="on the device with a seeded torch generator",
+                description="64 grids (octree/k-d, disk/ring/clumps, 1e4-1e6 leaves, built on the GPU), "
+                            "1e5-1e7 rays each")
+
+
+def _node_depths(H):
+    depth = np.zeros(H.n_nodes, np.int32)
+    nch = 8 if H.kind == 0 else 2
+    internal = np.nonzero(H.child_first >= 0)[0]
+    for nd in internal:  # breadth-first order: parents before children
+        c = H.child_first[nd]
+        depth[c:c + nch] = depth[nd] + 1
+    return depth
+
+
+def navigation_costs(H, ropes, seg_off, seg_cell, n_rays=20000):
+    """Exact per-crossing costs of finding the next leaf, from the emitted cell sequences of n_rays rays:
+    with neighbor lists, the position of the next leaf in the exit wall's list (records tested, tail ids
+    read) or the root descent when it is not among the stored entries; with ropes, the nodes visited below
+    the rope and the records tested.  Bytes: 96 per record, 4 per tail id, 16 (k-d) or 32 (octree) per node.
+    Crossings through an edge or corner (no unique shared wall) count as root descents for both."""
+    node_b = 32 if H.kind == 0 else 16
+    n = min(n_rays, seg_off.shape[0] - 1)
+    cells = seg_cell[:seg_off[n]].astype(np.int64)
+    ray_of = np.repeat(np.arange(n), np.diff(seg_off[:n + 1]))
+    same = ray_of[1:] == ray_of[:-1]
+    a, b = cells[:-1][same], cells[1:][same]
+    lo, hi = H.node_lo[H.leaf_node], H.node_hi[H.leaf_node]
+    depth = _node_depths(H)
+    leaf_depth = depth[H.leaf_node]
+    wall = np.full(a.shape[0], -1, np.int64)
+    nwalls = np.zeros(a.shape[0], np.int64)
+    for ax in range(3):
+        t = [x for x in range(3) if x != ax]
+        ov = np.ones(a.shape[0], bool)
+        for x in t:
+            ov &= np.minimum(hi[a, x], hi[b, x]) > np.maximum(lo[a, x], lo[b, x])
+        up = ov & (hi[a, ax] == lo[b, ax])
+        dn = ov & (lo[a, ax] == hi[b, ax])
+        wall = np.where(up, 2 * ax + 1, np.where(dn, 2 * ax, wall))
+        nwalls += up.astype(np.int64) + dn.astype(np.int64)
+    face = (wall >= 0) & (nwalls == 1)
+    # neighbor lists: position of b in list (a, wall)
+    rec_l = np.zeros(a.shape[0], np.float64)
+    tail_l = np.zeros(a.shape[0], np.float64)
+    node_l = np.zeros(a.shape[0], np.float64)
+    off = H.nbr_off
+    wsafe = np.maximum(wall, 0)
+    start = off[6 * a + wsafe]
+    cnt = off[6 * a + wsafe + 1] - start
+    head = face & (cnt > 0) & (H.nbr_id[np.minimum(start, H.nbr_id.shape[0] - 1)] == b)
+    rec_l[head] = 1
+    for i in np.nonzero(~head)[0]:
+        if face[i]:
+            lst = H.nbr_id[start[i]:start[i] + cnt[i]]
+            stored = lst if cnt[i] <= 16 else lst[:1]
+            hit = np.nonzero(stored == b[i])[0]
+            if hit.size:
+                p = int(hit[0])
+                rec_l[i], tail_l[i] = p + 1, p
+                continue
+            rec_l[i], tail_l[i] = stored.size + 1, max(0, stored.size - 1)
+        else:
+            rec_l[i] = 2
+        node_l[i] = leaf_depth[b[i]]
+    # ropes
+    r = ropes[a, wsafe]
+    rec_r = np.zeros(a.shape[0], np.float64)
+    node_r = np.zeros(a.shape[0], np.float64)
+    to_leaf = face & (r >= 0)
+    hit_leaf = to_leaf & (r == b)
+    rec_r[hit_leaf] = 1
+    internal = face & (r <= -2)
+    rn = np.where(internal, -2 - r, 0)
+    # b lies below the rope's node when the node's box contains b's box
+    inside = internal.copy()
+    for ax in range(3):
+        inside &= (H.node_lo[rn, ax] <= lo[b, ax]) & (hi[b, ax] <= H.node_hi[rn, ax])
+    rec_r[inside] = 1
+    node_r[inside] = leaf_depth[b[inside]] - depth[rn[inside]]
+    miss = ~(hit_leaf | inside)
+    rec_r[miss] = 2
+    node_r[miss] = leaf_depth[b[miss]] + np.where(internal[miss], leaf_depth[b[miss]] - depth[rn[miss]], 0)
+    m = max(1, a.shape[0])
+    lists = dict(records=float(rec_l.sum() / m), tail_ids=float(tail_l.sum() / m), nodes=float(node_l.sum() / m),
+                 head_hit=float(head.sum() / m))
+    lists["bytes"] = 96 * lists["records"] + 4 * lists["tail_ids"] + node_b * lists["nodes"]
+    rope = dict(records=float(rec_r.sum() / m), nodes=float(node_r.sum() / m),
+                rope_to_leaf=float(to_leaf.sum() / m), rope_to_leaf_hit=float(hit_leaf.sum() / m))
+    rope["bytes"] = 96 * rope["records"] + node_b * rope["nodes"]
+    return dict(transitions=int(a.shape[0]), edge_or_corner=float((~face).sum() / m), lists=lists, ropes=rope,
+                bytes_note="next-leaf lookups only; every crossing also reads nothing else for navigation")
+
+
+def measure_navigation(hg, torch, grids, O, K, flush, stream, reps=5):
+    """The rope walk against the neighbor-list walk on the step's grids and rays: the prepared optical-depth
+    walk (median of reps, L2 flushed), and the exact lookup costs from a sample of the emitted sequences."""
+    out = {}
+    for g in grids:
+        H = g["host"]
+        t0 = time.time()
+        ropes = hg.build_ropes(H)
+        rope_s = time.time() - t0
+        GR = hg.load_grid(H, nav="ropes", ropes=ropes)
+        res = {}
+        for name, G in (("lists", g["grid"]), ("ropes", GR)):
+            R = hg.prepare_rays(G, O, K)
+            tau, nc, st = R.trace()
+            ms = _events_ms(torch, stream, reps, flush, lambda: R.trace(out=(tau, nc, st)))
+            cr = int(nc.sum().item())
+            R.free()
+            res[name] = dict(walk_ms=round(ms, 4), gcross_per_s=cr / ms / 1e6)
+        costs = navigation_costs(H, ropes, g["seg_off_h"], g["seg_cell_h"])
+        for name in ("lists", "ropes"):
+            res[name].update(costs[name])
+        res.update(transitions_sampled=costs["transitions"], edge_or_corner=costs["edge_or_corner"],
+                   rope_build_s=round(rope_s, 2), device_bytes_lists=g["grid"].device_bytes,
+                   device_bytes_ropes=GR.device_bytes)
+        out[g["name"]] = res
+        del GR
+    return out
+
+
+def measure_interaction(hg, torch, grids, O, K, seed, flush, stream, reps=3):
+    """Interaction-point search on the step's grids and rays (kappa 200, tau_int = -ln u)."""
+    n = O.shape[0]
+    TI = torch.tensor(synth.interaction_depths(seed + 5, n), device=O.device)
+    peak, _ = _peak()
+    out = {}
+    for g in grids:
+        res = hg.find_interactions(g["grid"], O, K, TI, kappa=INTERACT_KAPPA)
+        ms = _events_ms(torch, stream, reps, flush,
+                        lambda: hg.find_interactions(g["grid"], O, K, TI, kappa=INTERACT_KAPPA, out=res))
+        cr = int(res[2].sum().item())
+        byt = BYTES_PER_CROSSING["fp64"] * cr + INTERACT_BYTES_PER_RAY * n
+        out[g["name"]] = dict(walk_ms=round(ms, 4), packets_per_s=n / ms * 1e3, gcross_per_s=cr / ms / 1e6,
+                              mean_ncross=cr / n, interacted=float((res[0] >= 0).float().mean().item()),
+                              roofline_frac=round(byt / (ms / 1e3) / 1e9 / peak, 4))
+    return out
 
 
 def run_torus(args):
@@ -1005,6 +1307,18 @@ def cpu_baseline(model, grids, o, k, pts, pa, pk, pl, w, sample: int = 200_000):
                        f"{len(trees)} grids: trace with emission, adjoint accumulation, density, Delta-tau paths")
 
 
+def torus_oracle_check(H, o, k, t64, t32, n: int = 20000):
+    """The torus rays' tau from the GPU (FP64 and FP32-Kahan) against the FP64 oracle on a sample."""
+    import oracle
+    T = oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho)
+    ref = oracle.trace(T, o[:n], k[:n], threads=os.cpu_count() or 1)["tau"]
+    pos = ref > 0
+    r64 = np.abs(t64[:n][pos] - ref[pos]) / ref[pos]
+    r32 = np.abs(t32[:n][pos] - ref[pos]) / ref[pos]
+    return dict(rays=n, fp64_max_rel=float(r64.max()), fp32k_max_rel=float(r32.max()),
+                fp32k_median_rel=float(np.median(r32)))
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -1056,6 +1370,8 @@ def main(argv=None):
     ap.add_argument("--no-matched", action="store_true",
                     help="skip the k-d tree built to the octree's leaf count (quality at equal N_cells)")
     ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the torus, 64-grid batch, rope and interaction measurements after the timed step")
     ap.add_argument("--kd-orientations", action="store_true",
                     help="also compare the cyclic and gradient-axis k-d trees (quality and walk speed, untimed)")
     args = ap.parse_args(argv)
