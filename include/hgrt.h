@@ -274,16 +274,19 @@ hg_status hg_load_grid_ropes(const hg_grid_desc *desc, const int32_t *ropes, int
  * the leaf itself, with a top-down descent when no listed neighbor
  * contains the exit point (edge and corner exits) or the list is long.
  *
- * FP64 arithmetic, no fused multiply-add, as in this contract:
+ * FP64 arithmetic as in this contract (fma: one rounding; every other
+ * multiply and add rounded on its own):
  *   invk_a = 1/d_a (d_a == +-0: axis a never exits);
  *   t_a = (wall_a - o_a) * invk_a for the wall ahead on each axis; exit at
  *   the smallest, ties to the lower axis; t_end wins only when smaller;
  *   exit times are never below the current time; ds = t_exit - t_cur and
  *   segments with ds == 0 are skipped (not emitted, not counted);
- *   exit point p_a = wall_a, p_b = o_b + d_b t_exit clamped to the leaf;
+ *   exit point p_a = wall_a, p_b = fma(d_b, t_exit, o_b) clamped to the
+ *   leaf (the entry point of an outside origin likewise);
  *   p lies in box [l, h] iff per axis l < p < h, p == l with d >= 0, or
  *   p == h with d < 0 (the domain's upper face also with d == 0);
- *   FP64 tau = kappa * (sum of rho*ds, left to right).
+ *   FP64 tau = kappa * S, S = fma(rho, ds, S) over the segments left to
+ *   right.
  * Directions are used as given (not normalised); s_max is in the same t. */
 typedef struct hg_trace_opts {
     int32_t precision;   /* HG_FP64 or HG_FP32K */
@@ -373,8 +376,8 @@ hg_status hg_trace_fill(const hg_grid *g, int64_t n, const double *o, const doub
 
 /* Interaction-point search (the step that follows the path in the Monte
  * Carlo loop of Sect. 2.3): each path is walked as in hg_trace_rays, in FP64,
- * and stops in the first recorded segment after which kappa * (sum of
- * rho*ds, left to right) >= tau_int[i].  Inside that leaf, entered at t_in
+ * and stops in the first recorded segment after which kappa * S >= tau_int[i]
+ * (S the contract's running sum fma(rho, ds, S)).  Inside that leaf, entered at t_in
  * and left at t_exit, the interaction time solves the linear growth of tau:
  *   a = tau_int - kappa*S_before, b = kappa*rho,
  *   t = t_in + a/b when a > 0 and b > 0, else t_in;  t = min(t, t_exit).

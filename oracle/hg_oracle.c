@@ -40,20 +40,21 @@
  *     (Sect. 3.2, Delta-tau metric).
  *
  * Arithmetic contract (all IEEE binary64, round to nearest, compiled with
- * -ffp-contract=off so that no multiply-add is fused):
+ * -ffp-contract=off so that only the explicit fma() calls fuse):
  *   invk_a = 1/k_a for k_a != 0 (a signed zero counts as zero);
  *   in leaf [lo, hi] the wall ahead on axis a is hi_a if k_a > 0 else lo_a,
  *   t_a = (wall_a - o_a) * invk_a; the exit is the smallest t_a, ties to the
  *   lowest axis, the path end wins only when strictly smaller, and the
  *   exit time is raised to the current time if rounding put it behind;
  *   ds = t_exit - t_cur, segments with ds == 0 are skipped;
- *   exit point: p_a = wall_a on the exit axis, p_b = o_b + k_b * t_exit on
+ *   the point at time t on axis b is fma(k_b, t, o_b) (one rounding); the
+ *   exit point is p_a = wall_a on the exit axis and the point at t_exit on
  *   the others, clamped to the leaf's [lo_b, hi_b];
  *   a point p belongs to box [l, h] for direction k iff on every axis
  *   l < p < h, or p == l and k >= 0, or p == h and k < 0 (the domain's
  *   upper face also accepts k == 0); descent takes the upper child iff
  *   p > c or (p == c and k >= 0);
- *   S = sum over segments of (rho * ds), left to right; tau = kappa * S.
+ *   S = fma(rho, ds, S) over the segments, left to right; tau = kappa * S.
  */
 #include <math.h>
 #include <stdint.h>
@@ -719,7 +720,7 @@ static int or_trace_one(const or_tree *T, const double *o, const double *k, int 
     } else {
         for (int a = 0; a < 3; a++) {
             if (a == entry) { p[a] = (k[a] > 0.0) ? dlo[a] : dhi[a]; continue; }
-            double v = o[a] + k[a] * t_start;
+            double v = fma(k[a], t_start, o[a]);
             if (v < dlo[a]) v = dlo[a];
             if (v > dhi[a]) v = dhi[a];
             p[a] = v;
@@ -752,7 +753,7 @@ static int or_trace_one(const or_tree *T, const double *o, const double *k, int 
                 seg_cell[*ncross] = (int32_t)cur;
                 seg_ds[*ncross] = ds;
             }
-            *S += T->rho[nd] * ds;
+            *S = fma(T->rho[nd], ds, *S);
             (*ncross)++;
         }
         t_cur = t_ex;
@@ -761,7 +762,7 @@ static int or_trace_one(const or_tree *T, const double *o, const double *k, int 
         if (wall == ((k[ax] > 0.0) ? dhi[ax] : dlo[ax])) return 0; /* leaves the domain */
         for (int b = 0; b < 3; b++) {
             if (b == ax) { p[b] = wall; continue; }
-            double v = o[b] + k[b] * t_ex;
+            double v = fma(k[b], t_ex, o[b]);
             if (v < lo[b]) v = lo[b];
             if (v > hi[b]) v = hi[b];
             p[b] = v;
@@ -849,7 +850,7 @@ static int or_interact_one(const or_tree *T, const double *o, const double *k, i
     } else {
         for (int a = 0; a < 3; a++) {
             if (a == entry) { p[a] = (k[a] > 0.0) ? dlo[a] : dhi[a]; continue; }
-            double v = o[a] + k[a] * t_start;
+            double v = fma(k[a], t_start, o[a]);
             if (v < dlo[a]) v = dlo[a];
             if (v > dhi[a]) v = dhi[a];
             p[a] = v;
@@ -877,7 +878,7 @@ static int or_interact_one(const or_tree *T, const double *o, const double *k, i
         double ds = t_ex - t_cur;
         if (ds != 0.0) {
             const double rho = T->rho[nd];
-            const double S_new = S + rho * ds;
+            const double S_new = fma(rho, ds, S);
             (*ncross)++;
             if (kappa * S_new >= tau_int) {
                 const double a = tau_int - kappa * S;
@@ -898,7 +899,7 @@ static int or_interact_one(const or_tree *T, const double *o, const double *k, i
         if (wall == ((k[ax] > 0.0) ? dhi[ax] : dlo[ax])) return 0;
         for (int b = 0; b < 3; b++) {
             if (b == ax) { p[b] = wall; continue; }
-            double v = o[b] + k[b] * t_ex;
+            double v = fma(k[b], t_ex, o[b]);
             if (v < lo[b]) v = lo[b];
             if (v > hi[b]) v = hi[b];
             p[b] = v;

@@ -13,7 +13,9 @@
 //
 // Every translation unit including this file is compiled with -fmad=false,
 // so each FP64 multiply and add below is rounded separately, as the
-// arithmetic contract in hgrt.h states.
+// arithmetic contract in hgrt.h states; the contract's fused operations (the
+// point o + k t on a path and the running sum of rho ds) are explicit
+// __fma_rn calls.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -356,7 +358,7 @@ __device__ __forceinline__ RayStart ray_setup(const DevGrid &G, const unsigned c
                 if (a == entry) {
                     v = dgt0(kk[a]) ? G.dlo[a] : G.dhi[a];
                 } else {
-                    v = oo[a] + kk[a] * ts;
+                    v = __fma_rn(kk[a], ts, oo[a]);
                     if (v < G.dlo[a]) v = G.dlo[a];
                     if (v > G.dhi[a]) v = G.dhi[a];
                 }
@@ -527,8 +529,8 @@ __device__ __forceinline__ void cand_first(const RayState &S, const Leaf &L, int
     const int b2 = (ax == 2) ? 1 : 2;
     const double ob1 = sel3(b1, S.o0, S.o1, S.o2), kb1 = sel3(b1, S.k0, S.k1, S.k2);
     const double ob2 = sel3(b2, S.o0, S.o1, S.o2), kb2 = sel3(b2, S.k0, S.k1, S.k2);
-    long long p1 = okey(ob1 + kb1 * tex);
-    long long p2 = okey(ob2 + kb2 * tex);
+    long long p1 = okey(__fma_rn(kb1, tex, ob1));
+    long long p2 = okey(__fma_rn(kb2, tex, ob2));
     const long long l1 = L.lo(b1), h1 = L.hi(b1), l2 = L.lo(b2), h2 = L.hi(b2);
     if (p1 < l1) p1 = l1;
     if (p1 > h1) p1 = h1;
@@ -816,7 +818,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                     // stop in the first segment after which kappa * S reaches tau_int; inside it tau grows
                     // linearly: t = t_in + (tau_int - kappa S_before) / (kappa rho), at most the exit time
                     const double rho = L.rho;
-                    const double s_new = acc + rho * ds;
+                    const double s_new = __fma_rn(rho, ds, acc);
                     if (io.kappa * s_new >= tint) {
                         const double a = tint - io.kappa * acc;
                         const double b = io.kappa * rho;
@@ -834,7 +836,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                 if (TAU) {
                     if (TPREC == HG_FP64) {
                         const double rho = io.rho_ext ? __ldg(io.rho_ext + S.cur) : L.rho;
-                        acc = acc + rho * ds;
+                        acc = __fma_rn(rho, ds, acc);
                     } else {
                         const float rho32 = io.rho_ext ? __double2float_rn(__ldg(io.rho_ext + S.cur)) : L.rho32;
                         const float kr32 = __fmul_rn(kappa32, rho32);
