@@ -54,10 +54,12 @@ STAGE_BYTES_PER_RAY = 4
 L2_FLUSH_BYTES = 512 << 20
 # what bounds the walk besides the copy bandwidth (see DESIGN, GB300-specific choices 1 and 4): random
 # gathers of 96-byte records from a 2 GB array sustained 13.2 G records/s (~1.27 TB/s) in a separate probe,
-# and FP64 add / multiply ran at ~500 G instructions/s; the FP64 walk issues 13 FP64 instructions per crossing
+# and FP64 add / multiply / fused multiply-add ran at ~500 G instructions/s; per crossing the walk issues 10
+# FP64 instructions (3 wall times of 2 each, 2 fused exit-point coordinates, ds, the fused sum; under
+# FP32-Kahan the sum leaves the FP64 pipe and the FP32 cast of ds joins it)
 RANDOM_GATHER_GBS = 1.27e3
 FP64_OPS_PER_S = 500e9
-FP64_OPS_PER_CROSSING = {"fp64": 13, "fp32k": 12}
+FP64_OPS_PER_CROSSING = {"fp64": 10, "fp32k": 10}
 
 
 # ----------------------------------------------------------------------------- distributed plumbing
@@ -334,6 +336,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    launch = {"min_blocks": args.min_blocks} if args.min_blocks else {}
     kev = []  # (start, end) events around the dominant kernel
     cev = []  # (start, end) events around the emission copy with the adjoint scatter
     gstreams = [torch.cuda.Stream(device=dev) for _ in grids]
@@ -357,7 +360,7 @@ def run_ours(args):
         out = {}
 
         def prep(g):
-            g["R"] = hg.prepare_rays(g["grid"], O, K)
+            g["R"] = hg.prepare_rays(g["grid"], O, K, **launch)
             g["grad"].zero_()
 
         def rest(g):
@@ -556,6 +559,7 @@ def run_ours(args):
                 dtype="f64" if prec == "fp64" else "f32+f64", data="synthetic",
                 config=dict(workload=args.workload, description=desc, rays_per_grid=n_rays, points=n_pts,
                             paths=n_paths, precision=prec, l2="flushed between steps (512 MB write)",
+                            min_blocks=args.min_blocks or 3,
                             grids=kern, kd_matched_to_octree=matched,
                             **({"kd_orientations": orient} if orient else {}), **extras),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
@@ -634,13 +638,26 @@ def measure_torus(hg, torch, dev, flush, stream, reps=3):
         G, O, K, W, grad=grad, grad_precision="fp32")))
     a32 = t32.double().cpu().numpy()
     a64 = t64.cpu().numpy()
+    same_counts = bool(torch.equal(nc, nc32))
+    # the same passes on the rope walk (records beyond L2: the walk is bound by record gathers)
+    t0 = time.time()
+    GR = hg.load_grid(H, nav="ropes")
+    rope_load_s = time.time() - t0
+    ropes = {}
+    for prec, out_ in (("fp32k", (t32, nc32, st)), ("fp64", (t64, nc, st))):
+        f = lambda: hg.trace_rays(GR, O, K, precision=prec, out=out_)  # noqa: E731
+        f()
+        ms = _events_ms(torch, stream, reps, flush, f)
+        ropes[prec] = dict(trace_ms=round(ms, 3), rays_per_s=n_rays / ms * 1e3, gcross_per_s=cr / ms / 1e6)
+    ropes["load_s"] = round(rope_load_s, 2)
+    del GR
     pos = a64 > 0
     rel = np.abs(a32[pos] - a64[pos]) / a64[pos]
     out = dict(leaves=G.n_leaves, rays=n_rays, mean_ncross=cr / n_rays, build_gpu_s=round(build_s, 2),
-               status_bits=bits, passes=passes, adjoint_fp32_ms=round(grad_ms, 3),
+               status_bits=bits, passes=passes, adjoint_fp32_ms=round(grad_ms, 3), rope_walk=ropes,
                fp32k_over_fp64_speed=passes["fp64"]["trace_ms"] / passes["fp32k"]["trace_ms"],
                fp32k_vs_fp64=dict(max_rel=float(rel.max()), median_rel=float(np.median(rel)),
-                                  identical_counts=bool(torch.equal(nc, nc32))),
+                                  identical_counts=same_counts),
                description="ring torus + 1000 clumps, k-d tree (mass 7e-7, tau 0.5, q 0.9, max level 10), "
                            "built on the GPU; 1e7 emission rays, one-shot hg_trace_rays per precision")
     del O, K, W, grad
@@ -1370,6 +1387,8 @@ def main(argv=None):
     ap.add_argument("--no-matched", action="store_true",
                     help="skip the k-d tree built to the octree's leaf count (quality at equal N_cells)")
     ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--min-blocks", type=int, choices=[3, 4], default=0,
+                    help="register budget of the step's walks: 3 (80 registers) or 4 (64) blocks of 256 per SM")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the torus, 64-grid batch, rope and interaction measurements after the timed step")
     ap.add_argument("--kd-orientations", action="store_true",
