@@ -291,13 +291,17 @@ hg_status hg_load_grid_ropes(const hg_grid_desc *desc, const int32_t *ropes, int
 typedef struct hg_trace_opts {
     int32_t precision;   /* HG_FP64 or HG_FP32K */
     int32_t block;       /* threads per block (32..256, multiple of 32); 0 = tuned or default */
-    int32_t smem_nodes;  /* top tree nodes staged in shared memory (clamped to 200 KB); -1 = tuned or default */
+    int32_t smem_nodes;  /* top tree nodes the walks stage in shared memory (clamped to 200 KB); -1 = tuned or
+                            default (64: the walk descends only after edge and corner exits and list misses, and
+                            shared memory is taken from the L1 that serves its record gathers).  The setup pass
+                            (first leaf of every ray) always stages the top 32 KB */
     int32_t schedule;    /* 0 = tuned or automatic; 1 = static ray stride; 2 = dynamic queue (warp-aggregated
                             counter) in input order; 3 = dynamic queue, rays with the most estimated
                             crossings first (automatic when there are fewer than 48 rays per
                             resident thread) */
-    int32_t min_blocks;  /* 0 = tuned or default (3); 3 or 4 resident 256-thread blocks per SM the
-                            kernel's register budget is cut for */
+    int32_t min_blocks;  /* 0 = tuned or default (4); 3 or 4 resident 256-thread blocks per SM the
+                            kernel's register budget is cut for (80 or 64 registers; each walking thread also
+                            keeps its ray's origin, direction and 1/d in 72 bytes of shared memory) */
     int32_t split;       /* HG_SPLIT_AUTO (0), HG_SPLIT_OFF or HG_SPLIT_FORCE; see below */
     int64_t max_steps;   /* per-ray step limit; 0 = 4 * n_leaves + 64 */
 } hg_trace_opts;

@@ -105,6 +105,7 @@ template <int PREC, int NAV>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
     __shared__ int64_t s_qbeg[kMaxBatch + 1];
     __shared__ int32_t s_perm[kMaxBatch];
+    __shared__ double s_geo[9 * 256];  // the walking threads' ray geometry (blocks of at most 256)
     for (int i = threadIdx.x; i <= A.n_grids; i += blockDim.x) s_qbeg[i] = A.qbeg[i];
     for (int i = threadIdx.x; i < A.n_grids; i += blockDim.x) s_perm[i] = A.perm[i];
     __syncthreads();
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
     io.tau = A.tau;
     io.ncross = A.ncross;
     io.status = A.status;
-    walk_loop<2, MODE_TAU, PREC, NAV>(src, io, nullptr, 0);
+    walk_loop<2, MODE_TAU, PREC, NAV>(src, io, nullptr, 0, s_geo);
 }
 
 }  // namespace hg

@@ -472,6 +472,13 @@ struct GridRays {
     }
 };
 
+// Dynamic shared memory of a walking launch: the top tree nodes, then the
+// threads' geometry slots (9 doubles per thread) at a 16-byte boundary.
+__host__ __device__ __forceinline__ size_t geo_offset(size_t node_bytes) { return (node_bytes + 15) / 16 * 16; }
+__host__ __device__ __forceinline__ size_t walk_smem(size_t node_bytes, int block) {
+    return geo_offset(node_bytes) + (size_t)block * 9 * sizeof(double);
+}
+
 // One persistent loop per thread (walk_loop): a lane whose ray has ended
 // takes the next one, and every iteration advances each lane by one record
 // load, so lanes never wait for the longest path in their warp.
@@ -536,7 +543,8 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.tau_int = A.tau_int;
     io.int_cell = A.int_cell;
     io.int_t = A.int_t;
-    walk_loop<KIND, MODE, PREC, NAV>(src, io, smem, A.n_smem);
+    walk_loop<KIND, MODE, PREC, NAV>(src, io, smem, A.n_smem,
+                                     reinterpret_cast<double *>(smem + geo_offset(A.n_smem * node_bytes)));
 }
 
 // ------------------------------------------------------------------ launch plumbing
@@ -583,8 +591,19 @@ int sm_count() {
     return n;
 }
 
-// Default launch shape: 256 threads, the top 2048 k-d nodes (32 KB) or
-// 1024 octree nodes (32 KB) in shared memory, persistent dynamic schedule.
+// Default launch shape of the walks: 256 threads, 4 blocks per SM (64
+// registers: the ray geometry sits in shared memory), the top 64 tree nodes
+// in shared memory -- the walk descends only after edge and corner exits
+// and list misses, and every byte of shared memory is taken from the L1
+// that serves its record gathers -- persistent dynamic schedule.  The setup
+// pass, which descends for every ray, stages the top 32 KB of the tree
+// (setup_nodes).
+constexpr int kWalkNodes = 64;
+int setup_nodes(const hg_grid *g) {
+    const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
+    return (int)std::min<int64_t>(g->d.n_nodes, (32 * 1024) / node_bytes);
+}
+
 hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precision, int &block, int &smem_nodes,
                        int &schedule, int &min_blocks, int64_t &max_steps, int &split) {
     precision = opts ? opts->precision : HG_FP64;
@@ -594,10 +613,9 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
     }
     const TuneEntry &T = g->tuned[precision];
     block = (opts && opts->block > 0) ? opts->block : (T.valid ? T.block : 256);
-    smem_nodes = (opts && opts->smem_nodes >= 0) ? opts->smem_nodes
-                                                  : (T.valid ? T.smem_nodes : (g->d.kind == HG_KDTREE ? 2048 : 1024));
+    smem_nodes = (opts && opts->smem_nodes >= 0) ? opts->smem_nodes : (T.valid ? T.smem_nodes : kWalkNodes);
     schedule = (opts && opts->schedule > 0) ? opts->schedule : (T.valid ? T.schedule : 0);
-    min_blocks = (opts && opts->min_blocks > 0) ? opts->min_blocks : (T.valid ? T.min_blocks : 3);
+    min_blocks = (opts && opts->min_blocks > 0) ? opts->min_blocks : (T.valid ? T.min_blocks : 4);
     max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 4 * g->d.n_leaves + 64;
     split = opts ? opts->split : HG_SPLIT_AUTO;
     if (split < HG_SPLIT_AUTO || split > HG_SPLIT_FORCE) {
@@ -625,6 +643,7 @@ hg_status resolve_opts(const hg_grid *g, const hg_trace_opts *opts, int &precisi
 }
 
 constexpr int kLatticeBytes = kWorkN * kWorkN * kWorkN * (int)sizeof(float);
+constexpr int kWalkSmemMax = 200 * 1024 + 256 * 9 * (int)sizeof(double);
 constexpr int kSetupSmemMax = 200 * 1024 + kLatticeBytes;
 
 void set_smem_limits() {
@@ -636,7 +655,7 @@ void set_smem_limits() {
                     for (int p = 0; p < mode_precs(m); p++)
                         for (int oc = 3; oc <= 4; oc++)
                             cudaFuncSetAttribute(pick_kernel(kd, m, p, oc, nav),
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kWalkSmemMax);
         // the setup pass also stages the work lattice after the nodes
         cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemMax);
         cudaFuncSetAttribute(setup_kernel<HG_OCTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSetupSmemMax);
@@ -669,7 +688,8 @@ struct hg_rays {
     int64_t max_steps = 0, threads = 0;
     bool dyn = false, ordered = false, splitting = false;
     bool traced = false;  // an optical-depth walk recorded the segments' crossing counts
-    size_t smem = 0;
+    size_t smem = 0;       // top tree nodes (the setup pass)
+    size_t walk_smem = 0;  // top tree nodes and the threads' ray geometry (the walks)
     unsigned char *scratch = nullptr;
     hg::RayStart *starts = nullptr;
     int64_t *order = nullptr;
@@ -718,9 +738,10 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     P.max_steps = max_steps;
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
     P.smem = (size_t)smem_nodes * node_bytes;
+    P.walk_smem = walk_smem(P.smem, block);
     int64_t blocks = 0;
     const KernelFn k0 = pick_kernel(g->d.kind, MODE_TAU, HG_FP64, min_blocks, g->d.nav);
-    hg_status hs = walk_blocks(k0, block, P.smem, n, blocks);
+    hg_status hs = walk_blocks(k0, block, P.walk_smem, n, blocks);
     if (hs != HG_OK) return hs;
     P.threads = blocks * block;
     // auto schedule: order by estimated work only when each resident thread
@@ -730,7 +751,7 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     P.ordered = (schedule == 3);
     P.splitting = P.ordered && allow_split && split != HG_SPLIT_OFF && g->d.work;
     if (P.splitting) {  // segments add queue items: the walks run every resident thread
-        hs = walk_blocks(k0, block, P.smem, INT64_MAX / 2, blocks);
+        hs = walk_blocks(k0, block, P.walk_smem, INT64_MAX / 2, blocks);
         if (hs != HG_OK) return hs;
         P.threads = blocks * block;
     }
@@ -783,13 +804,14 @@ hg_status make_plan(hg_rays &P, const hg_grid *g, int64_t n, const double *o, co
     e = cudaMemsetAsync(cnt, 0, count_bytes, stream);
     if (e != cudaSuccess) return cuda_err(e, "scratch reset");
     const int64_t sblocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
-    const size_t setup_smem = P.smem + ((P.ordered && !exact && g->d.work) ? kLatticeBytes : 0);
+    const int snodes = setup_nodes(g);
+    const size_t setup_smem = (size_t)snodes * node_bytes + ((P.ordered && !exact && g->d.work) ? kLatticeBytes : 0);
     if (g->d.kind == HG_KDTREE)
         setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, setup_smem, stream>>>(
-            g->d, n, o, d, smax, P.starts, smem_nodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
+            g->d, n, o, d, smax, P.starts, snodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
     else
         setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, setup_smem, stream>>>(
-            g->d, n, o, d, smax, P.starts, smem_nodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
+            g->d, n, o, d, smax, P.starts, snodes, P.counts, exact, P.ordered ? P.work_total : nullptr, P.work);
     note_launches(1);
     if (P.ordered) {
         order_kernel<<<(unsigned)sblocks, 256, 0, stream>>>(n, P.work, P.counts, P.counts + kBuckets, P.order);
@@ -1028,7 +1050,7 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
     const hg_grid *g = P.g;
     KernelFn k = pick_kernel(g->d.kind, mode, prec, P.min_blocks, g->d.nav);
     int64_t blocks = 0;
-    hg_status hs = walk_blocks(k, P.block, P.smem, P.splitting ? INT64_MAX / 2 : P.n, blocks);
+    hg_status hs = walk_blocks(k, P.block, P.walk_smem, P.splitting ? INT64_MAX / 2 : P.n, blocks);
     if (hs != HG_OK) return hs;
     A.G = g->d;
     A.n = P.n;
@@ -1069,7 +1091,7 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
         seg_base_kernel<<<cblocks, 256, 0, stream>>>(P.list, P.split_count, A.seg_off, P.part_nc, P.seg_base);
         note_launches(1);
     }
-    k<<<(unsigned)blocks, P.block, P.smem, stream>>>(A);
+    k<<<(unsigned)blocks, P.block, P.walk_smem, stream>>>(A);
     note_launches(1);
     e = cudaGetLastError();
     if (e == cudaSuccess && P.splitting) {
@@ -1796,9 +1818,10 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
     KernelFn k = pick_kernel(g->d.kind, MODE_TAU, prec, min_blocks, g->d.nav);
     const int node_bytes = g->d.kind == HG_KDTREE ? 16 : 32;
     const size_t smem = (size_t)smem_nodes * node_bytes;
+    const size_t wsmem = walk_smem(smem, block);
     cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (wsmem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kWalkSmemMax);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(setup_kernel<HG_KDTREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e == cudaSuccess)
@@ -1806,10 +1829,10 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
         if (e != cudaSuccess) return cuda_err(e, "shared-memory limit of the allocation-free walk");
     }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, wsmem);
     if (e != cudaSuccess) return cuda_err(e, "occupancy query");
     if (per_sm < 1) {
-        set_error("launch shape does not fit on an SM (block %d, %zu B shared)", block, smem);
+        set_error("launch shape does not fit on an SM (block %d, %zu B shared)", block, wsmem);
         return HG_EINVAL;
     }
     int64_t blocks = std::min<int64_t>((int64_t)per_sm * sm_count(), (n + block - 1) / block);
@@ -1818,13 +1841,15 @@ hg_status trace_rays_prealloc(const hg_grid *g, int64_t n, const double *o, cons
         if (e != cudaSuccess) return cuda_err(e, "counter reset");
     }
     const int64_t sblocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    const int snodes = setup_nodes(g);
+    const size_t ssmem = (size_t)snodes * node_bytes;
     if (g->d.kind == HG_KDTREE)
-        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes,
-                                                                         nullptr, nullptr, nullptr, nullptr);
+        setup_kernel<HG_KDTREE><<<(unsigned)sblocks, 256, ssmem, stream>>>(g->d, n, o, d, s_max, starts, snodes,
+                                                                          nullptr, nullptr, nullptr, nullptr);
     else
-        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, smem, stream>>>(g->d, n, o, d, s_max, starts, smem_nodes,
-                                                                         nullptr, nullptr, nullptr, nullptr);
-    k<<<(unsigned)blocks, block, smem, stream>>>(A);
+        setup_kernel<HG_OCTREE><<<(unsigned)sblocks, 256, ssmem, stream>>>(g->d, n, o, d, s_max, starts, snodes,
+                                                                          nullptr, nullptr, nullptr, nullptr);
+    k<<<(unsigned)blocks, block, wsmem, stream>>>(A);
     note_launches(2);
     e = cudaGetLastError();
     return e == cudaSuccess ? HG_OK : cuda_err(e, "trace launch");

@@ -154,9 +154,29 @@ __device__ __forceinline__ int32_t descend(const DevGrid &G, const unsigned char
     return -1;
 }
 
-// Per-ray walking state.
+// Per-ray walking state.  The ray's geometry -- origin o, direction k and
+// 1/k per axis -- sits in shared memory, in slots of the walking thread
+// (slot q of thread t at g[q * gs] with g = base + t, gs = threads per block,
+// so that a warp's accesses fall on consecutive words): it is read a few
+// times per crossing, and keeping its 18 registers out of the register file
+// lets four 256-thread blocks share an SM without spilling.
 struct RayState {
-    double o0, o1, o2, k0, k1, k2, ik0, ik1, ik2;
+    double *g;   // this thread's first geometry slot
+    int gs;      // slot stride
+    __device__ __forceinline__ double o(int a) const { return g[a * gs]; }
+    __device__ __forceinline__ double k(int a) const { return g[(3 + a) * gs]; }
+    __device__ __forceinline__ double ik(int a) const { return g[(6 + a) * gs]; }
+    __device__ __forceinline__ void set_geometry(const double *oo, const double *kk, double i0, double i1,
+                                                 double i2) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            g[a * gs] = (oo[a] == 0.0) ? 0.0 : oo[a];  // a signed-zero origin walks like +0
+            g[(3 + a) * gs] = kk[a];
+        }
+        g[6 * gs] = i0;
+        g[7 * gs] = i1;
+        g[8 * gs] = i2;
+    }
     long long ktend;   // key of the path end (KEY_INF: walk to the domain exit)
     long long ktstop;  // a path segment ends after the leaf whose exit time passes this (KEY_INF: none)
     long long ktcur;   // key of the current time
@@ -404,19 +424,12 @@ __device__ __forceinline__ int ray_resume(const double *__restrict__ o, const do
     *st = (uint32_t)c.y >> 8;
     if (c.x < 0) return WALK_END;
     if (SEGS && ((uint32_t)c.y & SG_SPLIT)) return WALK_SKIP;  // its segments do the work
-    S.ik0 = a.x;
-    S.ik1 = a.y;
-    S.ik2 = b.x;
     S.ktcur = __double_as_longlong(b.y);
     S.cur = c.x;
     S.sg = (uint32_t)c.y & 0xffu;
-    const double o0 = o[3 * r], o1 = o[3 * r + 1], o2 = o[3 * r + 2];
-    S.o0 = (o0 == 0.0) ? 0.0 : o0;
-    S.o1 = (o1 == 0.0) ? 0.0 : o1;
-    S.o2 = (o2 == 0.0) ? 0.0 : o2;
-    S.k0 = d[3 * r];
-    S.k1 = d[3 * r + 1];
-    S.k2 = d[3 * r + 2];
+    const double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
+    const double kk[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+    S.set_geometry(oo, kk, a.x, a.y, b.x);
     S.ktend = smax ? okey(smax[r]) : KEY_INF;
     if (SEGS) S.ktstop = KEY_INF;
     S.steps = 0;
@@ -441,16 +454,9 @@ __device__ __forceinline__ int seg_resume(const double *__restrict__ o, const do
     if (S.cur < 0) return WALK_END;
     const double2 *p = reinterpret_cast<const double2 *>(starts + r);
     const double2 i01 = __ldg(p), i2 = __ldg(p + 1);
-    S.ik0 = i01.x;
-    S.ik1 = i01.y;
-    S.ik2 = i2.x;
-    const double o0 = o[3 * r], o1 = o[3 * r + 1], o2 = o[3 * r + 2];
-    S.o0 = (o0 == 0.0) ? 0.0 : o0;
-    S.o1 = (o1 == 0.0) ? 0.0 : o1;
-    S.o2 = (o2 == 0.0) ? 0.0 : o2;
-    S.k0 = d[3 * r];
-    S.k1 = d[3 * r + 1];
-    S.k2 = d[3 * r + 2];
+    const double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
+    const double kk[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]};
+    S.set_geometry(oo, kk, i01.x, i01.y, i2.x);
     S.ktend = smax ? okey(smax[r]) : KEY_INF;
     S.steps = 0;
     return WALK_GO;
@@ -480,9 +486,9 @@ __device__ __forceinline__ int ray_exit(int32_t max_steps, RayState &S, const Le
     }
     S.steps++;
     const uint32_t sg = S.sg;
-    const long long ct0 = wall_time(dpos(sg, 0), dneg(sg, 0), L.lo0, L.hi0, S.o0, S.ik0);
-    const long long ct1 = wall_time(dpos(sg, 1), dneg(sg, 1), L.lo1, L.hi1, S.o1, S.ik1);
-    const long long ct2 = wall_time(dpos(sg, 2), dneg(sg, 2), L.lo2, L.hi2, S.o2, S.ik2);
+    const long long ct0 = wall_time(dpos(sg, 0), dneg(sg, 0), L.lo0, L.hi0, S.o(0), S.ik(0));
+    const long long ct1 = wall_time(dpos(sg, 1), dneg(sg, 1), L.lo1, L.hi1, S.o(1), S.ik(1));
+    const long long ct2 = wall_time(dpos(sg, 2), dneg(sg, 2), L.lo2, L.hi2, S.o(2), S.ik(2));
     // smallest time, ties to the lower axis; the path end only when strictly smaller
     long long kt = KEY_INF;
     int ax = -1;
@@ -527,8 +533,8 @@ __device__ __forceinline__ void cand_first(const RayState &S, const Leaf &L, int
     const int w = 2 * ax + (dpos(sg, ax) ? 1 : 0);
     const int b1 = (ax == 0) ? 1 : 0;
     const int b2 = (ax == 2) ? 1 : 2;
-    const double ob1 = sel3(b1, S.o0, S.o1, S.o2), kb1 = sel3(b1, S.k0, S.k1, S.k2);
-    const double ob2 = sel3(b2, S.o0, S.o1, S.o2), kb2 = sel3(b2, S.k0, S.k1, S.k2);
+    const double ob1 = S.o(b1), kb1 = S.k(b1);
+    const double ob2 = S.o(b2), kb2 = S.k(b2);
     long long p1 = okey(__fma_rn(kb1, tex, ob1));
     long long p2 = okey(__fma_rn(kb2, tex, ob2));
     const long long l1 = L.lo(b1), h1 = L.hi(b1), l2 = L.lo(b2), h2 = L.hi(b2);
@@ -718,8 +724,10 @@ struct WalkIO {
 //   PREC (MODE_ADJ): 0 = FP64 gradient atomics, 1 = FP32.
 //   PREC (MODE_TAUADJ): bit 0 the optical depth's (HG_FP32K), bit 1 the gradient's (FP32).
 //   NAV: 0 the grids hold neighbor lists, 1 ropes, 2 either (read per grid).
+// geo: shared memory for the geometry slots, 9 doubles per thread of the block.
 template <int KIND, int MODE, int PREC, int NAV, class Src>
-__device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem) {
+__device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsigned char *snodes, int n_smem,
+                                          double *geo) {
     constexpr bool SEGS = Src::kSegments;
     constexpr bool STAGE = (MODE == MODE_TAU_STAGE || MODE == MODE_TAUADJ_STAGE);
     constexpr bool INTER = (MODE == MODE_INTERACT);
@@ -732,6 +740,8 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
     int64_t ray = 0;
     int32_t max_steps = 0;
     RayState S;
+    S.g = geo + threadIdx.x;
+    S.gs = (int)blockDim.x;
     Leaf L;
     Cand C;
     double acc = 0.0;     // FP64 sum of rho*ds
