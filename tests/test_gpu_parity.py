@@ -736,6 +736,19 @@ def test_rope_walk_on_split_location_variants(hg, kind, plane, axis, dmax):
     _compare(hg, G, T, wo, wk, split="force")
 
 
+@pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
+def test_rope_walk_through_the_allocation_free_entry_point(hg, disk_grids, rope_grids, kind):
+    # the allocation-free optical-depth pass walks rope grids with the same kernels
+    model, grids, o, k = disk_grids
+    G, tree, H = rope_grids[kind]
+    ref = oracle.trace(tree, o, k, kappa=1.3)
+    tau, nc, st = hg.trace_rays_noalloc(G, _cuda(o), _cuda(k), kappa=1.3)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(_np(nc), ref["ncross"])
+    np.testing.assert_array_equal(_np(st), ref["status"])
+    _check_tau(_np(tau), ref["tau"], TAU_RTOL_FP64)
+
+
 def test_rope_and_list_grids_in_one_batch_match_oracle(hg):
     grids, trees, begins = _uneven_batch(hg, ropes=True)
     assert {g.nav for g in grids} == {hg.NAV_NEIGHBOR_LISTS, hg.NAV_ROPES}
