@@ -308,9 +308,9 @@ typedef struct hg_trace_opts {
 
 /* Path segments.  With schedule 3 (work-ordered queue), in hg_trace_rays,
  * hg_trace_rays_rho and hg_tau_gradient, a path whose estimated crossings
- * exceed 1.5 W is cut into segments of about W that separate threads walk
- * (W = max(32, estimated total / (4 x the launch's threads)); HG_SPLIT_FORCE:
- * W = 2, for testing).  Cuts lie at the middle of a leaf the path crosses,
+ * exceed max(64, A) is cut into at most 16 segments of about max(32, A/2)
+ * that separate threads walk (A = estimated total / the launch's threads;
+ * HG_SPLIT_FORCE: every path of more than 3, in pieces of 2, for testing).  Cuts lie at the middle of a leaf the path crosses,
  * deep inside it, so every segment follows the whole path's cell sequence:
  * crossing counts, statuses, emitted cells and gradients are those of the
  * unsplit walk; tau is the sum of the segments' partial sums, which differs
