@@ -988,8 +988,9 @@ __device__ __forceinline__ bool copy_staged_group(uint32_t e, int64_t cnt, int64
 
 // Emission from the staging pool: each ray's crossings (or its segments',
 // in path order with the counts of the staged walk) copied to its CSR slot,
-// eight lanes per unsplit ray and a warp per split ray; with GP >= 0 the
-// same pass scatters the adjoint (kappa w of the ray times each length).
+// the entries of 32 consecutive unsplit rays spread over a warp's lanes and a
+// warp per split ray; with GP >= 0 the same pass scatters the adjoint (kappa w
+// of the ray times each length).
 // Does nothing when the pool overflowed (the walks that follow then do the
 // emission and the adjoint).
 template <int GP, typename DS>
@@ -1007,24 +1008,79 @@ __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *
                                                      uint32_t gmul, uint32_t gmask) {
     if (*overflow) return;
     const unsigned long long keep = GP >= 0 ? l2_evict_last_policy() : 0ULL;
-    constexpr int G = 8;  // lanes per unsplit ray: four rays per warp in flight
-    const int lane = threadIdx.x & 31, g = lane & (G - 1);
-    const unsigned lanes = 0xffu << (lane & ~(G - 1));
-    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x / G);
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    for (int64_t r = g0; r < n; r += ngroups) {
-        if (starts[r].sg & SG_SPLIT) continue;
-        const int64_t b = seg_off[r], cnt = seg_off[r + 1] - b;
-        if (cnt <= 0) continue;
-        const double wk = GP >= 0 ? kappa * (double)__ldg(w + r) : 0.0;
-        const bool fit =
-            copy_staged_group<G, GP>(start_ray[r], cnt, b, cell, ds, next, out_cell, out_ds, cap, g, wk, grad, gmul,
-                                     gmask, keep);
-        if (!__all_sync(lanes, fit) && status && g == 0) status[r] |= HG_RAY_OVERFLOW;
-    }
-    // split rays: one warp each, segments in path order
+    const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // unsplit rays: a warp takes 32 consecutive rays and spreads their entries over its lanes, entry e of
+    // the window going to lane e mod 32 (a lane finds its ray by a binary search over the window's
+    // exclusive prefix of counts), so that short rays leave no lane idle and the CSR writes of
+    // consecutive entries are consecutive
+    for (int64_t r0 = w0 * 32; r0 < n; r0 += nw * 32) {
+        const int64_t r = r0 + lane;
+        int64_t cnt = 0, b = 0;
+        uint32_t first = 0;
+        double wk = 0.0;
+        if (r < n && !(starts[r].sg & SG_SPLIT)) {
+            b = seg_off[r];
+            cnt = seg_off[r + 1] - b;
+            if (cnt > 0) {
+                first = start_ray[r];
+                if (GP >= 0) wk = kappa * (double)__ldg(w + r);
+                if (status && b + cnt > cap) status[r] |= HG_RAY_OVERFLOW;
+            }
+        }
+        int64_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int64_t excl = incl - cnt;
+        const int64_t total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int64_t base = 0; base < total; base += 32) {
+            const int64_t e = base + lane;
+            // the largest window lane j with excl_j <= e owns entry e (lanes without entries share the
+            // next lane's prefix, so they are never the largest)
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int64_t ex = __shfl_sync(0xffffffffu, excl, j + step);
+                if (ex <= e) j += step;
+            }
+            const int64_t exj = __shfl_sync(0xffffffffu, excl, j);
+            const int64_t bj = __shfl_sync(0xffffffffu, b, j);
+            const uint32_t fj = __shfl_sync(0xffffffffu, first, j);
+            const double wkj = GP >= 0 ? __shfl_sync(0xffffffffu, wk, j) : 0.0;
+            if (e >= total) continue;
+            const int64_t k = e - exj;
+            // the walking thread appended the ray in its chunk chain: entries are contiguous up to the
+            // end of the first chunk, then continue in the chained chunks
+            int64_t pos = (int64_t)fj + k;
+            const int64_t avail = (int64_t)(kStageChunk - (fj & (kStageChunk - 1u)));
+            if (k >= avail) {
+                int64_t rest = k - avail;
+                uint32_t c = next[fj >> kStageShift];
+                while (rest >= (int64_t)kStageChunk) {
+                    c = next[c];
+                    rest -= kStageChunk;
+                }
+                pos = ((int64_t)c << kStageShift) + rest;
+            }
+            const int32_t cc = cell[pos];
+            const DS l = ds[pos];
+            if (bj + k < cap) {
+                out_cell[bj + k] = cc;
+                out_ds[bj + k] = l;
+            }
+            const uint32_t slot = ((uint32_t)cc * gmul) & gmask;
+            if (GP == 0) {
+                red_add_keep(static_cast<double *>(grad) + slot, wkj * (double)l, keep);
+            } else if (GP == 1) {
+                red_add_keep(static_cast<float *>(grad) + slot, __double2float_rn(wkj * (double)l), keep);
+            }
+        }
+    }
+    // split rays: one warp each, segments in path order
     const int64_t m = split_count ? (int64_t)*split_count : 0;
     for (int64_t i = w0; i < m; i += nw) {
         const SplitRec rec = list[i];
