@@ -294,7 +294,7 @@ typedef struct hg_trace_opts {
     int32_t smem_nodes;  /* top tree nodes the walks stage in shared memory (clamped to 200 KB); -1 = tuned or
                             default (64: the walk descends only after edge and corner exits and list misses, and
                             shared memory is taken from the L1 that serves its record gathers).  The setup pass
-                            (first leaf of every ray) always stages the top 32 KB */
+                            (first leaf of every ray) always stages the top 8 KB */
     int32_t schedule;    /* 0 = tuned or automatic; 1 = static ray stride; 2 = dynamic queue (warp-aggregated
                             counter) in input order; 3 = dynamic queue, rays with the most estimated
                             crossings first (automatic when there are fewer than 48 rays per
