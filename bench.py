@@ -54,11 +54,12 @@ STAGE_BYTES_PER_RAY = 4
 L2_FLUSH_BYTES = 512 << 20
 # what bounds the walk besides the copy bandwidth (see DESIGN, GB300-specific choices 1 and 4): random
 # gathers of 96-byte records from a 2 GB array sustained 13.2 G records/s (~1.27 TB/s) in a separate probe,
-# and FP64 add / multiply / fused multiply-add ran at ~500 G instructions/s; per crossing the walk issues 10
-# FP64 instructions (3 wall times of 2 each, 2 fused exit-point coordinates, ds, the fused sum; under
-# FP32-Kahan the sum leaves the FP64 pipe and the FP32 cast of ds joins it)
+# and FP64 add / fused multiply-add issued 16.5 G warp instructions/s (0.053 per cycle per SM) whether 32,
+# 16 or 1 lane was active, i.e. 528 G lane operations/s at full warps; per crossing the walk issues 10 FP64
+# instructions (3 wall times of 2 each, 2 fused exit-point coordinates, ds, the fused sum; under FP32-Kahan
+# the sum leaves the FP64 pipe and the FP32 cast of ds joins it)
 RANDOM_GATHER_GBS = 1.27e3
-FP64_OPS_PER_S = 500e9
+FP64_OPS_PER_S = 528e9
 FP64_OPS_PER_CROSSING = {"fp64": 10, "fp32k": 10}
 
 
@@ -350,7 +351,7 @@ def run_ours(args):
         for gs in gstreams:
             stream.wait_stream(gs)
 
-    def step(record=False):
+    def step(record=False, copy_out=None):
         # per grid: one setup (first leaf, work-ordered queue, path segments) for the emission rays;
         # one walk for the optical depth, counts and the staged emission; then the emission copy,
         # which also scatters the adjoint from the staged lengths, and the quality metrics.  The two
@@ -377,6 +378,8 @@ def run_ours(args):
             cell, ds, _ = R.emit_staged_gradient(off, W, kappa=1.0, grad=g["grad"], grad_precision="fp32",
                                                  capacity=cap, status=g["st"])
             g["off"], g["cell"], g["ds"] = off, cell, ds
+            if copy_out is not None:
+                copy_out(g)
             if record:
                 c1.record(gs)
                 cev.append((g["name"], c0, c1))
@@ -477,8 +480,9 @@ def run_ours(args):
                         fp64_issue_frac_of_peak=round(fp64_gcross * byte_per_cross / 1e9 / peak, 3),
                         random_gather_gbs=RANDOM_GATHER_GBS,
                         random_gather_frac_of_peak=round(RANDOM_GATHER_GBS / peak, 3),
-                        note=f"{FP64_OPS_PER_CROSSING[prec]} FP64 instructions per crossing at the ~500 G/s this GPU "
-                             "issues them bound the walk at fp64_issue_gcross_per_s, i.e. fp64_issue_frac_of_peak "
+                        note=f"{FP64_OPS_PER_CROSSING[prec]} FP64 instructions per crossing at the 528 G lane "
+                             "operations/s this GPU issues with full warps bound the walk at fp64_issue_gcross_per_s, "
+                             "i.e. fp64_issue_frac_of_peak "
                              "of the copy bandwidth in algorithmic bytes; random 96-byte record gathers from "
                              "beyond L2 sustain random_gather_gbs (separate probes); L2 serves part of the records"))
 
@@ -501,30 +505,57 @@ def run_ours(args):
                          torch.empty(g["cap"], dtype=torch.int32).pin_memory(),
                          torch.empty(g["cap"], dtype=g["ds"].dtype).pin_memory(),
                          torch.empty(g["grid"].n_leaves, dtype=torch.float32).pin_memory()])
+        # Each grid's results go out on a copy stream of its own as soon as its emission and gradient
+        # are complete, so that the device-to-host copies (bound by the host link, ~190 GB/s) overlap
+        # the rest of the step and the next step's work.  The next step rewrites
+        # tau, the counts and the gradient only after their copies (event `small`); the CSR arrays
+        # are new tensors every step, kept alive for the copy stream by record_stream.
+        cstreams = [torch.cuda.Stream(device=dev) for _ in grids]
+        small = [None] * len(grids)
+        hidx = {g["name"]: i for i, g in enumerate(grids)}
+
+        def copy_out(g):
+            i = hidx[g["name"]]
+            cs = cstreams[i]
+            cs.wait_stream(torch.cuda.current_stream())
+            h = hout[i]
+            with torch.cuda.stream(cs):
+                for dst, src in ((h[0], g["tau"]), (h[1], g["nc"]), (h[5], g["grad"]), (h[2], g["off"])):
+                    dst.copy_(src, non_blocking=True)
+                small[i] = torch.cuda.Event()
+                small[i].record(cs)
+                for dst, src in ((h[3], g["cell"]), (h[4], g["ds"])):
+                    src.record_stream(cs)
+                    dst.copy_(src[:dst.shape[0]], non_blocking=True)
+            g["off"].record_stream(cs)
+
         barrier(dist, dev)
         torch.cuda.synchronize()
-        es = []
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         for s in range(args.steps):
             flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
             O.copy_(ho, non_blocking=True)
             K.copy_(hk, non_blocking=True)
-            step()
-            for h, g in zip(hout, grids):
-                for dst, src in zip(h, (g["tau"], g["nc"], g["off"], g["cell"], g["ds"], g["grad"])):
-                    dst.copy_(src[:dst.shape[0]], non_blocking=True)
-            b.record(stream)
-            es.append((a, b))
+            for ev in small:
+                if ev is not None:
+                    stream.wait_event(ev)
+            step(copy_out=copy_out)
+        for cs in cstreams:
+            stream.wait_stream(cs)
+        b.record(stream)
         torch.cuda.synchronize()
         barrier(dist, dev)
-        e_ms = max_over_ranks(dist, sum(x.elapsed_time(y) for x, y in es), dev)
+        e_ms = max_over_ranks(dist, a.elapsed_time(b), dev)
         h2d = 2 * n_rays * 3 * 8
         d2h = sum(sum(t.numel() * t.element_size() for t in h) for h in hout)
         e2e = dict(value=sum_over_ranks(dist, rays_per_step * args.steps, dev) / (e_ms / 1e3), unit=UNIT,
                    h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                    copied="in: origins, directions; out per grid: tau, crossing counts, CSR offsets, "
-                          "emitted cells and lengths, gradient")
+                          "emitted cells and lengths, gradient",
+                   timing="one interval over all steps, L2 flushes included; each grid's device-to-host "
+                          "copies run on a stream of their own from the moment its emission is complete and "
+                          "overlap the rest of the step and the next step's work")
 
     # quality at equal cell counts (outside the timed region): a k-d tree whose mass threshold is bisected
     # until its leaf count is within 5 % of the octree's, with its Delta-rho and Delta-tau
@@ -559,7 +590,7 @@ def run_ours(args):
                 dtype="f64" if prec == "fp64" else "f32+f64", data="synthetic",
                 config=dict(workload=args.workload, description=desc, rays_per_grid=n_rays, points=n_pts,
                             paths=n_paths, precision=prec, l2="flushed between steps (512 MB write)",
-                            min_blocks=args.min_blocks or 3,
+                            min_blocks=args.min_blocks or 4,
                             grids=kern, kd_matched_to_octree=matched,
                             **({"kd_orientations": orient} if orient else {}), **extras),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),

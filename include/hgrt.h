@@ -299,9 +299,10 @@ typedef struct hg_trace_opts {
                             counter) in input order; 3 = dynamic queue, rays with the most estimated
                             crossings first (automatic when there are fewer than 48 rays per
                             resident thread) */
-    int32_t min_blocks;  /* 0 = tuned or default (4); 3 or 4 resident 256-thread blocks per SM the
-                            kernel's register budget is cut for (80 or 64 registers; each walking thread also
-                            keeps its ray's origin, direction and 1/d in 72 bytes of shared memory) */
+    int32_t min_blocks;  /* 0 = tuned or default (4; 3 for hg_find_interactions, whose walk needs more
+                            than 64 registers); 3 or 4 resident 256-thread blocks per SM the kernel's
+                            register budget is cut for (80 or 64 registers; each walking thread also keeps
+                            its ray's origin, direction and 1/d in 72 bytes of shared memory) */
     int32_t split;       /* HG_SPLIT_AUTO (0), HG_SPLIT_OFF or HG_SPLIT_FORCE; see below */
     int64_t max_steps;   /* per-ray step limit; 0 = 4 * n_leaves + 64 */
 } hg_trace_opts;
