@@ -49,8 +49,7 @@ struct TraceArgs {
     uint8_t *part_st;
     const int64_t *seg_base;  // emission offset of each path segment (fill walks)
     // emission staging (MODE_*_STAGE)
-    int32_t *stg_cell;
-    void *stg_ds;
+    void *stg_ent;
     uint32_t *stg_next;
     uint32_t stg_nchunks;
     unsigned long long *stg_ctr;
@@ -532,8 +531,7 @@ __global__ void __launch_bounds__(256, OCC) trace_kernel(const TraceArgs A) {
     io.part_last = A.part_last;
     io.part_st = A.part_st;
     io.seg_base = A.seg_base;
-    io.stg_cell = A.stg_cell;
-    io.stg_ds = A.stg_ds;
+    io.stg_ent = A.stg_ent;
     io.stg_next = A.stg_next;
     io.stg_nchunks = A.stg_nchunks;
     io.stg_ctr = A.stg_ctr;
@@ -708,8 +706,7 @@ struct hg_rays {
     // emission staging, allocated by the first staged trace
     unsigned char *stg = nullptr;
     size_t stg_bytes = 0;
-    int32_t *stg_cell = nullptr;
-    void *stg_ds = nullptr;
+    void *stg_ent = nullptr;
     uint32_t *stg_next = nullptr, *stg_start_ray = nullptr, *stg_start_seg = nullptr, *stg_overflow = nullptr;
     unsigned long long *stg_ctr = nullptr;
     uint32_t stg_nchunks = 0;
@@ -914,11 +911,11 @@ hg_status make_staging(hg_rays &P, int prec, int64_t per_ray, cudaStream_t strea
     entries = std::min<int64_t>(entries, (int64_t)0x7fffffff - kStageChunk);
     const int64_t nchunks = entries / kStageChunk;
     entries = nchunks * kStageChunk;
-    const size_t dsz = prec == HG_FP64 ? sizeof(double) : sizeof(float);
-    const size_t b_cell = al((size_t)entries * sizeof(int32_t)), b_ds = al((size_t)entries * dsz);
+    const size_t esz = prec == HG_FP64 ? 16 : 8;  // see stage_put
+    const size_t b_ent = al((size_t)entries * esz);
     const size_t b_next = al((size_t)nchunks * sizeof(uint32_t)), b_sr = al((size_t)P.n * sizeof(uint32_t));
     const size_t b_ss = al((size_t)std::max<int64_t>(P.seg_cap, 1) * sizeof(uint32_t)), b_ctr = 256;
-    const size_t total = b_cell + b_ds + b_next + b_sr + b_ss + b_ctr;
+    const size_t total = b_ent + b_next + b_sr + b_ss + b_ctr;
     if (total > P.stg_bytes) {
         if (P.stg) cudaFreeAsync(P.stg, stream);
         P.stg = nullptr;
@@ -931,10 +928,8 @@ hg_status make_staging(hg_rays &P, int prec, int64_t per_ray, cudaStream_t strea
         P.stg_bytes = total;
     }
     unsigned char *q = P.stg;
-    P.stg_cell = reinterpret_cast<int32_t *>(q);
-    q += b_cell;
-    P.stg_ds = q;
-    q += b_ds;
+    P.stg_ent = q;
+    q += b_ent;
     P.stg_next = reinterpret_cast<uint32_t *>(q);
     q += b_next;
     P.stg_start_ray = reinterpret_cast<uint32_t *>(q);
@@ -957,8 +952,7 @@ hg_status make_staging(hg_rays &P, int prec, int64_t per_ray, cudaStream_t strea
 // w of the ray; GP 0 FP64, 1 FP32 gradient; slot(c) = (c * gmul) & gmask),
 // for every entry, dropped or not.
 template <int G, int GP, typename DS>
-__device__ __forceinline__ bool copy_staged_group(uint32_t e, int64_t cnt, int64_t b,
-                                                  const int32_t *__restrict__ cell, const DS *__restrict__ ds,
+__device__ __forceinline__ bool copy_staged_group(uint32_t e, int64_t cnt, int64_t b, const void *__restrict__ ent,
                                                   const uint32_t *__restrict__ next, int32_t *out_cell, DS *out_ds,
                                                   int64_t cap, int g, double wk, void *grad, uint32_t gmul,
                                                   uint32_t gmask, unsigned long long keep) {
@@ -966,8 +960,9 @@ __device__ __forceinline__ bool copy_staged_group(uint32_t e, int64_t cnt, int64
     while (cnt > 0) {
         const int64_t piece = std::min<int64_t>(cnt, (int64_t)(kStageChunk - (e & (kStageChunk - 1u))));
         for (int64_t k = g; k < piece; k += G) {
-            const int32_t c = cell[e + k];
-            const DS l = ds[e + k];
+            int32_t c;
+            DS l;
+            stage_get(ent, (int64_t)e + k, c, l);
             if (b + k < cap) {
                 out_cell[b + k] = c;
                 out_ds[b + k] = l;
@@ -1003,7 +998,7 @@ __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *
                                                      const unsigned long long *split_count,
                                                      const uint32_t *__restrict__ start_seg,
                                                      const int32_t *__restrict__ part_nc,
-                                                     const int32_t *__restrict__ cell, const DS *__restrict__ ds,
+                                                     const void *__restrict__ ent,
                                                      const uint32_t *__restrict__ next, const uint32_t *overflow,
                                                      int32_t *out_cell, DS *out_ds, int64_t cap, uint8_t *status,
                                                      double kappa, const float *__restrict__ w, void *grad,
@@ -1068,8 +1063,9 @@ __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *
                 }
                 pos = ((int64_t)c << kStageShift) + rest;
             }
-            const int32_t cc = cell[pos];
-            const DS l = ds[pos];
+            int32_t cc;
+            DS l;
+            stage_get(ent, pos, cc, l);
             if (bj + k < cap) {
                 out_cell[bj + k] = cc;
                 out_ds[bj + k] = l;
@@ -1092,8 +1088,8 @@ __global__ void __launch_bounds__(256) gather_kernel(int64_t n, const RayStart *
         for (int j = 0; j < rec.count; j++) {
             const int64_t cnt = part_nc[rec.first + j];
             if (cnt > 0)
-                fit = copy_staged_group<32, GP>(start_seg[rec.first + j], cnt, b, cell, ds, next, out_cell, out_ds,
-                                                cap, lane, wk, grad, gmul, gmask, keep) &&
+                fit = copy_staged_group<32, GP>(start_seg[rec.first + j], cnt, b, ent, next, out_cell, out_ds, cap,
+                                                lane, wk, grad, gmul, gmask, keep) &&
                       fit;
             b += cnt;
         }
@@ -1132,8 +1128,7 @@ hg_status walk_plan(hg_rays &P, int mode, int prec, TraceArgs A, cudaStream_t st
         A.seg_base = P.seg_base;
     }
     if (mode == MODE_TAU_STAGE || mode == MODE_TAUADJ_STAGE) {
-        A.stg_cell = P.stg_cell;
-        A.stg_ds = P.stg_ds;
+        A.stg_ent = P.stg_ent;
         A.stg_next = P.stg_next;
         A.stg_nchunks = P.stg_nchunks;
         A.stg_ctr = P.stg_ctr;
@@ -1651,9 +1646,9 @@ static hg_status emit_staged(const char *name, hg_rays *r, const int64_t *seg_of
     const unsigned long long *sc = r->splitting ? r->split_count : nullptr;
 #define HG_GATHER(GP, DS)                                                                                          \
     gather_kernel<GP, DS><<<(unsigned)gblocks, 256, 0, s>>>(                                                     \
-        r->n, r->starts, seg_off, r->stg_start_ray, r->list, sc, r->stg_start_seg, r->part_nc, r->stg_cell,     \
-        static_cast<const DS *>(r->stg_ds), r->stg_next, r->stg_overflow, seg_cell, static_cast<DS *>(seg_ds), \
-        seg_capacity, ray_status, kappa, w, B.grad, B.gmul, B.gmask)
+        r->n, r->starts, seg_off, r->stg_start_ray, r->list, sc, r->stg_start_seg, r->part_nc, r->stg_ent,      \
+        r->stg_next, r->stg_overflow, seg_cell, static_cast<DS *>(seg_ds), seg_capacity, ray_status, kappa, w,  \
+        B.grad, B.gmul, B.gmask)
     if (r->stg_prec == HG_FP64) {
         if (gp < 0)
             HG_GATHER(-1, double);

@@ -666,8 +666,30 @@ enum {
 // walks to its own chain of chunks, taking a new chunk from a global
 // counter when one fills.  Entry positions are stored shifted by one chunk
 // (position p is entry p - kStageChunk) so that 0 means "no chunk yet".
+// An entry keeps its cell beside its length, written with one vector store:
+// 16 bytes {ds, cell, unused} after an FP64 walk, 8 bytes {ds, cell} after
+// an FP32-Kahan one.  A thread's stores then complete a 32-byte sector
+// every two (FP64) or four crossings; with separate cell and length arrays
+// a sector of cells took eight, and sectors that L2 evicted half-written
+// reached DRAM twice.
 constexpr int kStageShift = 7;
 constexpr uint32_t kStageChunk = 1u << kStageShift;
+__device__ __forceinline__ void stage_put(void *ent, uint32_t e, int32_t c, double ds) {
+    reinterpret_cast<int4 *>(ent)[e] = make_int4(__double2loint(ds), __double2hiint(ds), c, 0);
+}
+__device__ __forceinline__ void stage_put(void *ent, uint32_t e, int32_t c, float ds) {
+    reinterpret_cast<int2 *>(ent)[e] = make_int2(__float_as_int(ds), c);
+}
+__device__ __forceinline__ void stage_get(const void *ent, int64_t e, int32_t &c, double &ds) {
+    const int4 v = __ldg(reinterpret_cast<const int4 *>(ent) + e);
+    ds = __hiloint2double(v.y, v.x);
+    c = v.z;
+}
+__device__ __forceinline__ void stage_get(const void *ent, int64_t e, int32_t &c, float &ds) {
+    const int2 v = __ldg(reinterpret_cast<const int2 *>(ent) + e);
+    ds = __int_as_float(v.x);
+    c = v.y;
+}
 struct WalkIO {
     const double *o;
     const double *d;
@@ -702,8 +724,7 @@ struct WalkIO {
     uint8_t *part_st = nullptr;    // partial status bits
     const int64_t *seg_base = nullptr;  // emission offset of each segment (MODE_FILL)
     // staging (MODE_*_STAGE)
-    int32_t *stg_cell = nullptr;
-    void *stg_ds = nullptr;              // f64 or f32 (HG_FP32K) entries
+    void *stg_ent = nullptr;             // staged entries (FP64 or HG_FP32K layout, see stage_put)
     uint32_t *stg_next = nullptr;        // chunk -> next chunk of the same thread
     uint32_t stg_nchunks = 0;
     unsigned long long *stg_ctr = nullptr;
@@ -887,11 +908,10 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
                             else
                                 io.stg_start_ray[ray] = e;
                         }
-                        io.stg_cell[e] = S.cur;
                         if (TPREC == HG_FP64)
-                            static_cast<double *>(io.stg_ds)[e] = ds;
+                            stage_put(io.stg_ent, e, S.cur, ds);
                         else
-                            static_cast<float *>(io.stg_ds)[e] = __double2float_rn(ds);
+                            stage_put(io.stg_ent, e, S.cur, __double2float_rn(ds));
                         sp++;
                     }
                 }

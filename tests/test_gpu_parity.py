@@ -619,7 +619,9 @@ def _same_interactions(hg, grid, tree, o, k, ti, smax=None, kappa=1.0, **opt):
     return ref
 
 
-@pytest.mark.parametrize("shape", [dict(), dict(schedule=1), dict(schedule=2, block=128)], ids=["auto", "s1", "s2"])
+# the default launch shape of the search is 3 blocks per SM (80 registers); min_blocks=4 runs the 64-register build
+@pytest.mark.parametrize("shape", [dict(), dict(schedule=1), dict(schedule=2, block=128), dict(min_blocks=4)],
+                         ids=["auto", "s1", "s2", "occ4"])
 @pytest.mark.parametrize("kind", [0, 1], ids=["octree", "kd"])
 def test_interaction_points_match_oracle(hg, disk_grids, kind, shape):
     model, grids, o, k = disk_grids
