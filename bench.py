@@ -566,7 +566,7 @@ def run_ours(args):
     if world == 1 and args.kd_orientations and args.workload == "disk-1e6":
         orient = kd_orientations(hg, torch, model, O, K, P, PA, PK, PL, RT, TT, flush, stream)
 
-    # the benchmark spec's other configurations, after the timed step (single GPU)
+    # the other configurations: the torus k-d tree, the 64-grid batch, navigation and interaction (one GPU)
     extras = {}
     torus_check = None
     if world == 1 and not args.no_extras and args.workload == "disk-1e6":
@@ -626,8 +626,8 @@ def _peak():
 
 
 # ----------------------------------------------------------------------------- sub-workloads of the default line
-# Measured after the timed disk step (outside it) and reported under config: the benchmark spec's other
-# configurations -- the ~1e7-leaf torus (FP32-Kahan against FP64), the 64-grid batch (one graph-replayed
+# Measured after the timed disk step (outside it) and reported under config: the other configurations
+# -- the ~1e7-leaf torus (FP32-Kahan against FP64), the 64-grid batch (one graph-replayed
 # launch against 64 launches), the rope walk against the neighbor-list walk, the interaction search.
 
 def _events_ms(torch, stream, reps, flush, fn):
