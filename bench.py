@@ -506,13 +506,19 @@ def run_ours(args):
                          torch.empty(g["cap"], dtype=g["ds"].dtype).pin_memory(),
                          torch.empty(g["grid"].n_leaves, dtype=torch.float32).pin_memory()])
         # Each grid's results go out on a copy stream of its own as soon as its emission and gradient
-        # are complete, so that the device-to-host copies (bound by the host link, ~190 GB/s) overlap
-        # the rest of the step and the next step's work.  The next step rewrites
-        # tau, the counts and the gradient only after their copies (event `small`); the CSR arrays
-        # are new tensors every step, kept alive for the copy stream by record_stream.
+        # are complete, so that the device-to-host copies (bound by the host link, ~190 GB/s, one copy
+        # at a time) overlap the rest of the step and the next step's work.  Steps alternate between
+        # two sets of the tau, count and gradient buffers, so that a step never waits for the copies
+        # of the step before (a set is rewritten two steps later, after the event `small` of its
+        # copies); the CSR arrays are new tensors every step, kept alive for the copy stream by
+        # record_stream.
         cstreams = [torch.cuda.Stream(device=dev) for _ in grids]
-        small = [None] * len(grids)
         hidx = {g["name"]: i for i, g in enumerate(grids)}
+        for g in grids:
+            g["alt"] = dict(tau=torch.empty_like(g["tau"]), nc=torch.empty_like(g["nc"]),
+                            grad=torch.zeros_like(g["grad"]))
+        small = [[None, None] for _ in grids]  # per grid and buffer set: the end of its small copies
+        cur = [0]
 
         def copy_out(g):
             i = hidx[g["name"]]
@@ -522,8 +528,9 @@ def run_ours(args):
             with torch.cuda.stream(cs):
                 for dst, src in ((h[0], g["tau"]), (h[1], g["nc"]), (h[5], g["grad"]), (h[2], g["off"])):
                     dst.copy_(src, non_blocking=True)
-                small[i] = torch.cuda.Event()
-                small[i].record(cs)
+                ev = torch.cuda.Event()
+                ev.record(cs)
+                small[i][cur[0]] = ev
                 for dst, src in ((h[3], g["cell"]), (h[4], g["ds"])):
                     src.record_stream(cs)
                     dst.copy_(src[:dst.shape[0]], non_blocking=True)
@@ -537,9 +544,12 @@ def run_ours(args):
             flush.zero_()
             O.copy_(ho, non_blocking=True)
             K.copy_(hk, non_blocking=True)
-            for ev in small:
-                if ev is not None:
-                    stream.wait_event(ev)
+            cur[0] = s % 2
+            for i, g in enumerate(grids):
+                for key in ("tau", "nc", "grad"):
+                    g[key], g["alt"][key] = g["alt"][key], g[key]
+                if small[i][cur[0]] is not None:
+                    stream.wait_event(small[i][cur[0]])
             step(copy_out=copy_out)
         for cs in cstreams:
             stream.wait_stream(cs)
@@ -555,7 +565,8 @@ def run_ours(args):
                           "emitted cells and lengths, gradient",
                    timing="one interval over all steps, L2 flushes included; each grid's device-to-host "
                           "copies run on a stream of their own from the moment its emission is complete and "
-                          "overlap the rest of the step and the next step's work")
+                          "overlap the rest of the step and the next step's work (two alternating sets of "
+                          "the tau, count and gradient buffers)")
 
     # quality at equal cell counts (outside the timed region): a k-d tree whose mass threshold is bisected
     # until its leaf count is within 5 % of the octree's, with its Delta-rho and Delta-tau
