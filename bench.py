@@ -915,6 +915,8 @@ def run_torus(args):
     dist = dist_init(world, True)
     desc, maker = WORKLOADS[args.workload]
     model, grids, n_rays, seed = maker(hg)
+    if args.rays:
+        n_rays = args.rays  # a smaller ray batch on the full grid (profiling)
     g = grids[0]
     t0 = time.time()
     G = hg.load_grid(g["host"], validate=args.validate)
@@ -1429,6 +1431,8 @@ def main(argv=None):
     ap.add_argument("--no-matched", action="store_true",
                     help="skip the k-d tree built to the octree's leaf count (quality at equal N_cells)")
     ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--rays", type=int, default=0,
+                    help="torus-1e7 only: rays per step instead of 1e7 (a smaller case of the same kernel for ncu)")
     ap.add_argument("--min-blocks", type=int, choices=[3, 4], default=0,
                     help="register budget of the step's walks: 3 (80 registers) or 4 (64) blocks of 256 per SM")
     ap.add_argument("--no-extras", action="store_true",
