@@ -214,7 +214,8 @@ typedef struct hg_grid_info {
     int64_t n_nodes, n_leaves;
     int64_t n_tail;         /* stored neighbor entries beyond each wall's first */
     int64_t device_bytes;   /* HBM held by the grid */
-    int64_t long_walls;     /* walls whose list is longer than the scan limit (searched top-down) */
+    int64_t long_walls;     /* walls whose list is longer than the scan limit (searched top-down from the
+                               wall's rope node, the deepest node across the wall covering it) */
     double lo[3], hi[3];
     int32_t nav;            /* HG_NAV_NEIGHBOR_LISTS or HG_NAV_ROPES: how the next leaf is found */
     int32_t reserved;
@@ -272,7 +273,10 @@ hg_status hg_load_grid_ropes(const hg_grid_desc *desc, const int32_t *ropes, int
  * first leaf comes from a top-down descent; every later one from the exit
  * wall's neighbor list (Sect. 2.3), the list's first entry being stored in
  * the leaf itself, with a top-down descent when no listed neighbor
- * contains the exit point (edge and corner exits) or the list is long.
+ * contains the exit point (edge and corner exits) or the list is long (for
+ * a long list the descent starts at the deepest node across the wall that
+ * covers the whole wall, and falls back to the root if the leaf found there
+ * does not hold the exit point).
  *
  * FP64 arithmetic as in this contract (fma: one rounding; every other
  * multiply and add rounded on its own):

@@ -382,6 +382,19 @@ hg_status load_grid_impl(const hg_grid_desc *desc, const int32_t *ropes, int32_t
         std::vector<hg::LeafRec> rec((size_t)nl);
         std::vector<int32_t> tail;
         int64_t long_walls = 0;
+        // A list too long to scan keeps one tail entry instead: the wall's rope node (the deepest
+        // node across the wall that covers the whole face), where the top-down search for the exit
+        // point can start instead of the root.
+        std::vector<int32_t> wall_ropes;
+        if (!ropes) {
+            bool any_long = false;
+            for (int64_t i = 0; i < 6 * nl && !any_long; i++) any_long = D.nbr_off[i + 1] - D.nbr_off[i] > kScanLimit;
+            if (any_long) {
+                wall_ropes.resize((size_t)(6 * nl));
+                hg_status st = hg_build_ropes(desc, 0, wall_ropes.data());
+                if (st != HG_OK) return st;
+            }
+        }
         const double *dhi = D.node_hi;
         for (int64_t i = 0; i < nl; i++) {
             hg::LeafRec &R = rec[i];
@@ -414,6 +427,8 @@ hg_status load_grid_impl(const hg_grid_desc *desc, const int32_t *ropes, int32_t
                 if (cnt >= 2 && cnt <= kScanLimit) {
                     for (int64_t e = b0 + 1; e < b1; e++) tail.push_back(D.nbr_id[e]);
                 } else if (cnt > kScanLimit) {
+                    const int32_t r = wall_ropes[(size_t)(6 * i + w)];
+                    tail.push_back(r <= -2 ? -2 - r : -1);  // an internal node; -1: search from the root
                     long_walls++;
                 }
             }

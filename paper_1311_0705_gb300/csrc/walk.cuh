@@ -574,7 +574,9 @@ __device__ __forceinline__ bool cand_contains(uint32_t sg, const Leaf &L, const 
 }
 
 // Where the rest of the exit wall's list is: read from the leaf being left
-// (only needed when the head does not contain the exit point).
+// (only needed when the head does not contain the exit point).  A list
+// longer than scan_limit keeps a single tail entry, the wall's rope node:
+// then C.ntail = -2 and C.off points at it.
 __device__ __forceinline__ void cand_tail_info(const DevGrid &G, uint32_t sg, Cand &C) {
     const int w = 2 * C.ax + (dpos(sg, C.ax) ? 1 : 0);
     const unsigned char *rec = reinterpret_cast<const unsigned char *>(G.rec + C.prev);
@@ -587,12 +589,12 @@ __device__ __forceinline__ void cand_tail_info(const DevGrid &G, uint32_t sg, Ca
         const int c = v < 4 ? (int)((c03 >> (8 * v)) & 255u) : (int)((c45 >> (8 * (v - 4))) & 255u);
         if (v == w) {
             cw = c;
-        } else if (c >= 2 && c <= G.scan_limit) {
-            off += (uint32_t)(c - 1);
+        } else if (c >= 2) {
+            off += c <= G.scan_limit ? (uint32_t)(c - 1) : 1u;
         }
     }
     C.off = off;
-    C.ntail = (cw >= 2 && cw <= G.scan_limit) ? cw - 1 : 0;
+    C.ntail = (cw >= 2 && cw <= G.scan_limit) ? cw - 1 : (cw > G.scan_limit ? -2 : 0);
 }
 
 // No listed neighbor contains the exit point: an exit point on the domain
@@ -606,17 +608,18 @@ __device__ __forceinline__ bool cand_leaves_domain(const DevGrid &G, uint32_t sg
 }
 
 // Top-down location of the exit point: the wall on the exit axis (the near
-// bound of the listed neighbor L) and the clamped point on the others.
+// bound of the listed neighbor L) and the clamped point on the others, from
+// the root or from node start.
 template <int KIND>
 __device__ __forceinline__ int32_t cand_descend(const DevGrid &G, const unsigned char *snodes, int n_smem,
-                                                uint32_t sg, const Leaf &L, const Cand &C) {
+                                                uint32_t sg, const Leaf &L, const Cand &C, int32_t start = 0) {
     const int ax = C.ax;
     const long long wall = dpos(sg, ax) ? L.lo(ax) : L.hi(ax);
     const int b1 = (ax == 0) ? 1 : 0;
     const long long q0 = (ax == 0) ? wall : (b1 == 0 ? C.p1 : C.p2);
     const long long q1 = (ax == 1) ? wall : (b1 == 1 ? C.p1 : C.p2);
     const long long q2 = (ax == 2) ? wall : C.p2;
-    return descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg);
+    return descend<KIND>(G, snodes, n_smem, q0, q1, q2, sg, start);
 }
 
 // Rope walk: the leaf below the rope's internal node C.id that holds the
@@ -824,21 +827,29 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             const DevGrid &G = *Gp;
             load_leaf(G.rec, C.id, L);
             if (C.mode == CAND_TEST && !cand_contains(S.sg, L, C)) {
-                if (C.ntail < 0) cand_tail_info(G, S.sg, C);
+                if (C.ntail == -1) cand_tail_info(G, S.sg, C);
                 if (C.e < C.ntail) {
                     C.id = __ldg(G.tail + C.off + C.e);
                     C.e++;
                     continue;
                 }
                 if (cand_leaves_domain(G, S.sg, C)) goto finish;
-                // edge or corner exit, or a long list: locate the exit point top-down
-                const int32_t j = cand_descend<KIND>(G, snodes, n_smem, S.sg, L, C);
+                // edge or corner exit, or a long list: locate the exit point top-down -- for a long list
+                // first below the wall's rope node, the leaf found there then tested like a listed
+                // neighbor (a point on the face's edge may belong outside the node); else from the root
+                int32_t start = 0;
+                if (C.ntail == -2) {
+                    start = __ldg(G.tail + C.off);
+                    C.ntail = 0;
+                    if (start < 0) start = 0;
+                }
+                const int32_t j = cand_descend<KIND>(G, snodes, n_smem, S.sg, L, C, start);
                 if (j < 0) {
                     st = HG_RAY_LOST;
                     goto finish;
                 }
                 C.id = j;
-                C.mode = CAND_ENTER;
+                C.mode = start > 0 ? CAND_TEST : CAND_ENTER;
                 continue;
             }
             S.cur = C.id;
