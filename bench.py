@@ -782,8 +782,8 @@ def _node_depths(H):
 def navigation_costs(H, ropes, seg_off, seg_cell, n_rays=20000):
     """Exact per-crossing costs of finding the next leaf, from the emitted cell sequences of n_rays rays:
     with neighbor lists, the position of the next leaf in the exit wall's list (records tested, tail ids
-    read) or the root descent when it is not among the stored entries; with ropes, the nodes visited below
-    the rope and the records tested.  Bytes: 96 per record, 4 per tail id, 16 (k-d) or 32 (octree) per node.
+    read), or, for a list too long to store whose head misses, the descent below the wall's rope node;
+    with ropes, the nodes visited below the rope and the records tested.  Bytes: 96 per record, 4 per tail id, 16 (k-d) or 32 (octree) per node.
     Crossings through an edge or corner (no unique shared wall) count as root descents for both."""
     node_b = 32 if H.kind == 0 else 16
     n = min(n_rays, seg_off.shape[0] - 1)
@@ -826,6 +826,11 @@ def navigation_costs(H, ropes, seg_off, seg_cell, n_rays=20000):
                 rec_l[i], tail_l[i] = p + 1, p
                 continue
             rec_l[i], tail_l[i] = stored.size + 1, max(0, stored.size - 1)
+            if cnt[i] > 16:  # the rope node kept in the tail slot, then the descent below it
+                rn_i = -2 - int(ropes[a[i], wall[i]])
+                tail_l[i] = 1
+                node_l[i] = leaf_depth[b[i]] - depth[rn_i] if ropes[a[i], wall[i]] <= -2 else leaf_depth[b[i]]
+                continue
         else:
             rec_l[i] = 2
         node_l[i] = leaf_depth[b[i]]
