@@ -650,6 +650,68 @@ def test_interaction_points_path_ends_and_bad_inputs(hg, disk_grids, kind):
     _same_interactions(hg, grid, tree, o, kk, rng.exponential(0.1, 2000))
 
 
+# ----------------------------------------------------------------------------- long neighbor lists
+# A wall with more than 16 neighbors keeps only its list head and its rope node on the device: a path whose exit
+# point misses the head is located top-down from the rope node (the leaf found there tested like a listed
+# neighbor, the root searched when it fails).  The clumpy torus makes such walls at small sizes.
+
+LONG_LIST_GRIDS = [(synth.TREE_OCTREE, 3e-4, 6), (synth.TREE_KD, 1e-4, 8)]
+
+
+def _long_wall_rays(H, tree, seed, per_wall=40):
+    """Rays from inside each leaf that has a long wall to points of that wall: uniform on the face, on the
+    corners of its neighbors, and on the face's own edges and corners."""
+    cnt = np.diff(H.nbr_off)
+    idx = np.nonzero(cnt > 16)[0]
+    rng = np.random.default_rng(seed)
+    o, k = [], []
+    for i in idx:
+        a, w = int(i // 6), int(i % 6)
+        ax = w // 2
+        lo, hi = tree.leaf_lo[a], tree.leaf_hi[a]
+        nb = H.nbr_id[H.nbr_off[i]:H.nbr_off[i + 1]]
+        for j in range(per_wall):
+            p = lo + rng.random(3) * (hi - lo)
+            q = lo + rng.random(3) * (hi - lo)
+            if j % 4 == 1:  # a corner of a listed neighbor
+                c = int(nb[rng.integers(0, nb.size)])
+                q = np.where(rng.random(3) < 0.5, tree.leaf_lo[c], tree.leaf_hi[c])
+            elif j % 4 == 2:  # the face's own edges and corners
+                q = np.where(rng.random(3) < 0.5, lo, hi)
+            q[ax] = hi[ax] if w % 2 else lo[ax]
+            d = q - p
+            n = np.linalg.norm(d)
+            if n == 0.0:
+                continue
+            o.append(p)
+            k.append(d / n)
+    return np.array(o), np.array(k)
+
+
+@pytest.mark.parametrize("kind,dmax,level", LONG_LIST_GRIDS, ids=["octree", "kd"])
+def test_long_lists_search_from_the_rope_node(hg, kind, dmax, level):
+    model = synth.workload_torus_1e7()[0]
+    bp = synth.BuildParams(kind=kind, delta_max=dmax, max_level=level, seed=synth.BASE_SEED)
+    H = hg.build_grid(model, bp)
+    G = hg.load_grid(H, validate=True)
+    assert G.long_walls > 0
+    tree = oracle.wrap_tree(H.kind, H.node_lo, H.node_hi, H.child_first, H.node_leaf, H.leaf_rho)
+    o, k = _long_wall_rays(H, tree, 90 + kind)
+    assert o.shape[0] > 400
+    for shape in (dict(), dict(split="force"), dict(schedule=1, smem_nodes=0)):
+        _compare(hg, G, tree, o, k, **shape)
+    _compare(hg, G, tree, o, k, precision="fp32k")
+    e, d = synth.emission_rays(91 + kind, 20000)
+    _compare(hg, G, tree, e, d)
+    ref = oracle.interact(tree, o, k, np.random.default_rng(kind).exponential(0.5, o.shape[0]), kappa=3.0)
+    cell, t, nc, st = hg.find_interactions(G, _cuda(o), _cuda(k),
+                                           _cuda(np.random.default_rng(kind).exponential(0.5, o.shape[0])),
+                                           kappa=3.0)
+    np.testing.assert_array_equal(_np(cell), ref["cell"])
+    np.testing.assert_array_equal(_np(t), ref["t"])
+    np.testing.assert_array_equal(_np(nc), ref["ncross"])
+
+
 # ----------------------------------------------------------------------------- ropes
 # The rope walk (hg_load_grid_ropes): the next leaf from the exit wall's rope, located below the rope's node
 # when that is not a leaf, instead of from the neighbor list.  Same contract, so the same oracle.
