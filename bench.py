@@ -351,6 +351,8 @@ def run_ours(args):
         for gs in gstreams:
             stream.wait_stream(gs)
 
+    IN = {"O": O, "K": K}  # the step's input rays (the end-to-end loop alternates two sets)
+
     def step(record=False, copy_out=None):
         # per grid: one setup (first leaf, work-ordered queue, path segments) for the emission rays;
         # one walk for the optical depth, counts and the staged emission; then the emission copy,
@@ -361,7 +363,7 @@ def run_ours(args):
         out = {}
 
         def prep(g):
-            g["R"] = hg.prepare_rays(g["grid"], O, K, **launch)
+            g["R"] = hg.prepare_rays(g["grid"], IN["O"], IN["K"], **launch)
             g["grad"].zero_()
 
         def rest(g):
@@ -539,11 +541,32 @@ def run_ours(args):
         barrier(dist, dev)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # the inputs of the next step are copied in on a stream of their own while the current step
+        # runs, into the other of two sets of ray buffers (once the step that last read it is done)
+        Oset, Kset = [O, torch.empty_like(O)], [K, torch.empty_like(K)]
+        h2d = torch.cuda.Stream(device=dev)
+        ready, done = [None, None], [None, None]
+
+        def copy_in(x):
+            if done[x] is not None:
+                h2d.wait_event(done[x])
+            with torch.cuda.stream(h2d):
+                Oset[x].copy_(ho, non_blocking=True)
+                Kset[x].copy_(hk, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(h2d)
+                ready[x] = ev
+
         a.record(stream)
+        h2d.wait_stream(stream)
+        copy_in(0)
         for s in range(args.steps):
+            x = s % 2
+            if s + 1 < args.steps:
+                copy_in(1 - x)
             flush.zero_()
-            O.copy_(ho, non_blocking=True)
-            K.copy_(hk, non_blocking=True)
+            stream.wait_event(ready[x])
+            IN["O"], IN["K"] = Oset[x], Kset[x]
             cur[0] = s % 2
             for i, g in enumerate(grids):
                 for key in ("tau", "nc", "grad"):
@@ -551,9 +574,13 @@ def run_ours(args):
                 if small[i][cur[0]] is not None:
                     stream.wait_event(small[i][cur[0]])
             step(copy_out=copy_out)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            done[x] = ev
         for cs in cstreams:
             stream.wait_stream(cs)
         b.record(stream)
+        IN["O"], IN["K"] = O, K
         torch.cuda.synchronize()
         barrier(dist, dev)
         e_ms = max_over_ranks(dist, a.elapsed_time(b), dev)
@@ -566,7 +593,8 @@ def run_ours(args):
                    timing="one interval over all steps, L2 flushes included; each grid's device-to-host "
                           "copies run on a stream of their own from the moment its emission is complete and "
                           "overlap the rest of the step and the next step's work (two alternating sets of "
-                          "the tau, count and gradient buffers)")
+                          "the tau, count and gradient buffers); each step's rays are copied in on their own "
+                          "stream while the step before runs (two alternating sets of ray buffers)")
 
     # quality at equal cell counts (outside the timed region): a k-d tree whose mass threshold is bisected
     # until its leaf count is within 5 % of the octree's, with its Delta-rho and Delta-tau
