@@ -538,9 +538,6 @@ def run_ours(args):
                     dst.copy_(src[:dst.shape[0]], non_blocking=True)
             g["off"].record_stream(cs)
 
-        barrier(dist, dev)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # the inputs of the next step are copied in on a stream of their own while the current step
         # runs, into the other of two sets of ray buffers (once the step that last read it is done)
         Oset, Kset = [O, torch.empty_like(O)], [K, torch.empty_like(K)]
@@ -557,40 +554,52 @@ def run_ours(args):
                 ev.record(h2d)
                 ready[x] = ev
 
-        a.record(stream)
-        h2d.wait_stream(stream)
-        copy_in(0)
-        for s in range(args.steps):
-            x = s % 2
-            if s + 1 < args.steps:
-                copy_in(1 - x)
-            flush.zero_()
-            stream.wait_event(ready[x])
-            IN["O"], IN["K"] = Oset[x], Kset[x]
-            cur[0] = s % 2
-            for i, g in enumerate(grids):
-                for key in ("tau", "nc", "grad"):
-                    g[key], g["alt"][key] = g["alt"][key], g[key]
-                if small[i][cur[0]] is not None:
-                    stream.wait_event(small[i][cur[0]])
-            step(copy_out=copy_out)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-            done[x] = ev
-        for cs in cstreams:
-            stream.wait_stream(cs)
-        b.record(stream)
-        IN["O"], IN["K"] = O, K
-        torch.cuda.synchronize()
+        def e2e_steps(nsteps):
+            # nsteps end-to-end steps; returns their span in ms (CUDA events on the main stream)
+            for lst in [ready, done] + small:
+                lst[0] = lst[1] = None
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h2d.wait_stream(stream)
+            copy_in(0)
+            for s in range(nsteps):
+                x = s % 2
+                if s + 1 < nsteps:
+                    copy_in(1 - x)
+                flush.zero_()
+                stream.wait_event(ready[x])
+                IN["O"], IN["K"] = Oset[x], Kset[x]
+                cur[0] = x
+                for i, g in enumerate(grids):
+                    for key in ("tau", "nc", "grad"):
+                        g[key], g["alt"][key] = g["alt"][key], g[key]
+                    if small[i][x] is not None:
+                        stream.wait_event(small[i][x])
+                step(copy_out=copy_out)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                done[x] = ev
+            for cs in cstreams:
+                stream.wait_stream(cs)
+            b.record(stream)
+            IN["O"], IN["K"] = O, K
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+
+        e2e_steps(max(2, args.warmup))  # untimed: the allocator's pools settle for the alternating buffers
         barrier(dist, dev)
-        e_ms = max_over_ranks(dist, a.elapsed_time(b), dev)
+        torch.cuda.synchronize()
+        span = e2e_steps(args.steps)
+        barrier(dist, dev)
+        e_ms = max_over_ranks(dist, span, dev)
         h2d = 2 * n_rays * 3 * 8
         d2h = sum(sum(t.numel() * t.element_size() for t in h) for h in hout)
         e2e = dict(value=sum_over_ranks(dist, rays_per_step * args.steps, dev) / (e_ms / 1e3), unit=UNIT,
                    h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                    copied="in: origins, directions; out per grid: tau, crossing counts, CSR offsets, "
                           "emitted cells and lengths, gradient",
-                   timing="one interval over all steps, L2 flushes included; each grid's device-to-host "
+                   timing="one interval over all steps, after warm-up steps of the same loop, L2 flushes "
+                          "included; each grid's device-to-host "
                           "copies run on a stream of their own from the moment its emission is complete and "
                           "overlap the rest of the step and the next step's work (two alternating sets of "
                           "the tau, count and gradient buffers); each step's rays are copied in on their own "
