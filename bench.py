@@ -713,6 +713,18 @@ def measure_torus(hg, torch, dev, flush, stream, reps=3):
         passes[prec] = dict(trace_ms=round(ms, 3), rays_per_s=n_rays / ms * 1e3, gcross_per_s=cr / ms / 1e6,
                             achieved_gbs=round(byt / (ms / 1e3) / 1e9, 1),
                             roofline_frac=round(byt / (ms / 1e3) / 1e9 / peak, 4))
+    # the same rays prepared once (setup, queue, segments) and walked per precision: the walk alone
+    prepared = {}
+    R = hg.prepare_rays(G, O, K)
+    prepared["prepare_ms"] = round(_events_ms(torch, stream, reps, flush, lambda: hg.prepare_rays(G, O, K).free()), 3)
+    for prec, out_ in (("fp32k", (t32, nc32, st)), ("fp64", (t64, nc, st))):
+        f = lambda: R.trace(kappa=1.0, precision=prec, out=out_)  # noqa: E731
+        f()
+        ms = _events_ms(torch, stream, reps, flush, f)
+        byt = BYTES_PER_CROSSING[prec] * cr + BYTES_PER_RAY[prec] * n_rays
+        prepared[prec] = dict(walk_ms=round(ms, 3), gcross_per_s=cr / ms / 1e6,
+                              roofline_frac=round(byt / (ms / 1e3) / 1e9 / peak, 4))
+    R.free()
     grad_ms = _events_ms(torch, stream, 1, flush, lambda: (grad.zero_(), hg.tau_gradient(
         G, O, K, W, grad=grad, grad_precision="fp32")))
     a32 = t32.double().cpu().numpy()
@@ -733,7 +745,8 @@ def measure_torus(hg, torch, dev, flush, stream, reps=3):
     pos = a64 > 0
     rel = np.abs(a32[pos] - a64[pos]) / a64[pos]
     out = dict(leaves=G.n_leaves, rays=n_rays, mean_ncross=cr / n_rays, build_gpu_s=round(build_s, 2),
-               status_bits=bits, passes=passes, adjoint_fp32_ms=round(grad_ms, 3), rope_walk=ropes,
+               status_bits=bits, passes=passes, prepared_walks=prepared, adjoint_fp32_ms=round(grad_ms, 3),
+               rope_walk=ropes,
                fp32k_over_fp64_speed=passes["fp64"]["trace_ms"] / passes["fp32k"]["trace_ms"],
                fp32k_vs_fp64=dict(max_rel=float(rel.max()), median_rel=float(np.median(rel)),
                                   identical_counts=same_counts),
