@@ -451,7 +451,8 @@ hg_status hg_rays_trace_gradient(hg_rays *r, double kappa, const double *rho, in
 /* Single-pass emission.  hg_rays_trace_stage is hg_rays_trace (w NULL) or
  * hg_rays_trace_gradient (w non-NULL) that also stages every emitted (cell,
  * ds) in a pool owned by the handle: about stage_per_ray entries per ray
- * (0 = 64) plus one 128-entry chunk per walking thread, kept until
+ * (0 = 64) plus one 128-entry chunk per walking thread, 16 bytes per entry
+ * after an FP64 trace and 8 after an HG_FP32K one, kept until
  * hg_rays_free.  hg_rays_emit_staged then copies each ray's crossings to
  * seg_cell / seg_ds at seg_off (hg_scan_offsets over the staged ncross) --
  * the same arrays hg_rays_fill writes, without a second walk.  When the pool
