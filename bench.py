@@ -591,6 +591,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         span = e2e_steps(args.steps)
         barrier(dist, dev)
+        # every step walks the same rays: the host copies of the last step must be the device results
+        for h, g in zip(hout, grids):
+            if not (torch.equal(h[1], g["nc"].cpu()) and torch.equal(h[2], g["off"].cpu()) and
+                    torch.equal(h[3], g["cell"][:h[3].shape[0]].cpu()) and torch.equal(h[0], g["tau"].cpu())):
+                raise RuntimeError(f"end-to-end host copies differ from the device results on {g['name']}")
         e_ms = max_over_ranks(dist, span, dev)
         h2d = 2 * n_rays * 3 * 8
         d2h = sum(sum(t.numel() * t.element_size() for t in h) for h in hout)
