@@ -522,8 +522,9 @@ struct Cand {
     int32_t ax;     // exit axis
     int32_t e;      // next tail entry to try
     int32_t ntail;  // tail entries of the exit wall's list (-1: not read yet)
-    uint32_t off;   // where they start
+    uint32_t off;   // where they start (KEEP: the left leaf's nbr_base until they are read)
     int32_t prev;   // the leaf being left
+    uint32_t c03, c45;  // KEEP: the left leaf's list lengths, so that a missed head re-reads no record
     long long p1, p2;  // keys of the exit point on the two other axes (b1 < b2)
 };
 
@@ -532,7 +533,9 @@ struct Cand {
 // neighbor to test, the head of the exit wall's list stored in the leaf --
 // or, on a grid loaded with ropes, the wall's rope: a leaf to test, or
 // (C.id <= -2) the internal node -2 - C.id to search below (cand_rope).
-template <int NAV>
+// KEEP (the interaction search, which has registers to spare at 3 blocks per
+// SM): keep the left leaf's list lengths and tail base in the candidate.
+template <int NAV, bool KEEP>
 __device__ __forceinline__ void cand_first(const RayState &S, const Leaf &L, int ax, double tex, Cand &C) {
     const uint32_t sg = S.sg;
     const int w = 2 * ax + (dpos(sg, ax) ? 1 : 0);
@@ -559,6 +562,11 @@ __device__ __forceinline__ void cand_first(const RayState &S, const Leaf &L, int
     C.e = 0;
     C.ntail = -1;
     C.prev = S.cur;
+    if (KEEP) {
+        C.off = L.base;
+        C.c03 = L.c03;
+        C.c45 = L.c45;
+    }
     C.p1 = p1;
     C.p2 = p2;
 }
@@ -577,13 +585,22 @@ __device__ __forceinline__ bool cand_contains(uint32_t sg, const Leaf &L, const 
 // (only needed when the head does not contain the exit point).  A list
 // longer than scan_limit keeps a single tail entry, the wall's rope node:
 // then C.ntail = -2 and C.off points at it.
+template <bool KEEP>
 __device__ __forceinline__ void cand_tail_info(const DevGrid &G, uint32_t sg, Cand &C) {
     const int w = 2 * C.ax + (dpos(sg, C.ax) ? 1 : 0);
-    const unsigned char *rec = reinterpret_cast<const unsigned char *>(G.rec + C.prev);
-    const double2 d = __ldg(reinterpret_cast<const double2 *>(rec + 48));
-    const int4 f = __ldg(reinterpret_cast<const int4 *>(rec + 80));
-    const uint32_t c03 = (uint32_t)f.z, c45 = (uint32_t)f.w;
-    uint32_t off = (uint32_t)((unsigned long long)__double_as_longlong(d.y) >> 32);
+    uint32_t c03, c45, off;
+    if (KEEP) {
+        c03 = C.c03;
+        c45 = C.c45;
+        off = C.off;
+    } else {
+        const unsigned char *rec = reinterpret_cast<const unsigned char *>(G.rec + C.prev);
+        const double2 d = __ldg(reinterpret_cast<const double2 *>(rec + 48));
+        const int4 f = __ldg(reinterpret_cast<const int4 *>(rec + 80));
+        c03 = (uint32_t)f.z;
+        c45 = (uint32_t)f.w;
+        off = (uint32_t)((unsigned long long)__double_as_longlong(d.y) >> 32);
+    }
     int cw = 0;
     for (int v = 0; v <= w; v++) {
         const int c = v < 4 ? (int)((c03 >> (8 * v)) & 255u) : (int)((c45 >> (8 * (v - 4))) & 255u);
@@ -827,7 +844,7 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             const DevGrid &G = *Gp;
             load_leaf(G.rec, C.id, L);
             if (C.mode == CAND_TEST && !cand_contains(S.sg, L, C)) {
-                if (C.ntail == -1) cand_tail_info(G, S.sg, C);
+                if (C.ntail == -1) cand_tail_info<INTER>(G, S.sg, C);
                 if (C.e < C.ntail) {
                     C.id = __ldg(G.tail + C.off + C.e);
                     C.e++;
@@ -943,9 +960,9 @@ __device__ __forceinline__ void walk_loop(Src &src, const WalkIO &io, const unsi
             }
             if (r == WALK_GO) {
                 if (NAV == 0 || (NAV == 2 && G.nav == HG_NAV_NEIGHBOR_LISTS))
-                    cand_first<0>(S, L, ax, tex, C);
+                    cand_first<0, INTER>(S, L, ax, tex, C);
                 else
-                    cand_first<1>(S, L, ax, tex, C);
+                    cand_first<1, INTER>(S, L, ax, tex, C);
                 if (NAV != 0 && C.mode == CAND_ROPE) {  // a rope to an internal node: the exit point's leaf below it
                     C.id = rope_descend<KIND>(G, snodes, n_smem, S.sg, L.lo(ax), L.hi(ax), C);
                     C.mode = CAND_TEST;
